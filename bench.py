@@ -1,0 +1,312 @@
+"""Benchmark: Newton steps per second on truncated power series in multiple
+double arithmetic, one GB300 per rank.
+
+Workload (default): quad double, real, n = 64 equations and unknowns,
+16 monomials of 2..8 distinct variables per equation plus 64 x_i, series of
+degree d = 31, planted solution; one "step" is one Newton step (evaluation
+and differentiation, Householder QR of A0 and its inverse, forward
+substitution over the 32 coefficient blocks, update and norms).  Every group
+of 7 steps restarts from the start series, the config's step count.
+
+Output: one JSON line (rank 0).  ``value`` is Newton steps/s over all ranks
+from CUDA events around each timed step (inputs resident in HBM, L2 flushed
+between steps); ``e2e`` times whole solves through the public API with the
+start series copied from pinned host memory and the solution copied back;
+``roofline`` reports the phase with the largest share of device time against
+the FP64 pipe peak; ``cpu_baseline`` times the CPU oracle on a bounded sample.
+
+``--impl reference`` times the CPU oracle (the plain multiple double
+implementation the tests check the GPU against) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2301_12659_gb300 import flops as F  # noqa: E402
+from paper_2301_12659_gb300 import workloads as wl  # noqa: E402
+
+# FP64 pipe peak of one GB300: 152 SMs x 1.684 FP64 lane operations per clock
+# per SM (measured: one warp instruction per 64 cycles per sub-partition,
+# ~76 with all four busy) x the 2070 MHz maximum SM clock.
+FP64_LANES_PER_CLK_PER_SM = 1.684
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_OPS = NUM_SMS * FP64_LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
+
+METRIC = "Newton steps/s (qd, n=64, d=31)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=70)
+    ap.add_argument("--warmup", type=int, default=7)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="qd-real-n64-d31", choices=sorted(wl.CONFIGS))
+    ap.add_argument("--e2e-solves", type=int, default=5)
+    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm and CPU baseline: the CPU oracle
+# ---------------------------------------------------------------------------
+def oracle_sample(cfg, nsteps):
+    """Time `nsteps` oracle Newton steps on the workload (host cores)."""
+    from oracle import oracle
+    s, xstar, x0 = wl.planted_system(cfg)
+    s.cst = oracle.planted_constant(s, xstar)
+    t0 = time.perf_counter()
+    oracle.newton(s, x0, nsteps)
+    dt = time.perf_counter() - t0
+    return dt, oracle.get_threads()
+
+
+def run_reference(args, cfg):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle import oracle
+    s, xstar, x0 = wl.planted_system(cfg)
+    s.cst = oracle.planted_constant(s, xstar)
+    x = x0
+    for i in range(args.warmup):
+        x, _ = oracle.newton(s, x0 if i % cfg.steps == 0 else x, 1)
+    times = []
+    x = x0
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        x, _ = oracle.newton(s, x0 if i % cfg.steps == 0 else x, 1)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    v = args.steps / total
+    cores = oracle.get_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(cfg),
+        "data": "synthetic", "config": config_dict(cfg, args),
+        "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle Newton steps of the workload on {cores} host threads"},
+        "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def dtype_name(cfg):
+    return {1: "f64", 2: "f64x2 (double double)", 4: "f64x4 (quad double)", 8: "f64x8 (octo double)"}[cfg.K] + \
+        (" complex" if cfg.C == 2 else "")
+
+
+def config_dict(cfg, args):
+    return {"workload": cfg.name, "limbs": cfg.K, "complex": cfg.C == 2, "n": cfg.n, "degree": cfg.d,
+            "monomials_per_equation": cfg.mono_per_eq, "vars_per_monomial": [cfg.kmin, cfg.kmax],
+            "newton_steps_per_solve": cfg.steps, "parallelism": f"replicas x{args.gpus}",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, cfg):
+    import torch
+    from paper_2301_12659_gb300 import mdnewton as md
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    s, xstar, x0 = wl.planted_system(cfg)
+    s.cst = None
+    nw = md.Newton(s)
+    # constant term planting x*: minus the system at x* (evaluated here)
+    cst = -nw.evaluate(xstar, want_A=False)
+    nw.set_constant(cst)
+    x0_dev = torch.as_tensor(x0, device=dev)
+    # correctness check of this run: recover the plant within the tolerance
+    nw.set_series(x0_dev)
+    nw.newton(cfg.steps)
+    xs_dev = torch.as_tensor(xstar, device=dev)
+    x = nw.series()
+    diff = (x - xs_dev)[0].abs().max().item()  # leading limbs: a coarse check only
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+
+    def one_step(i):
+        if i % cfg.steps == 0:
+            nw.set_series(x0_dev)
+        st, done, _ = md.mdn_newton(nw.ctx, 1, 0.0)
+        if st != md.MDN_OK:
+            raise md.MdnError(st, md.mdn_last_error(nw.ctx))
+
+    for i in range(args.warmup):
+        one_step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    md.mdn_profile(nw.ctx, 1)
+    evs = []
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_step(i)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    _, phase_ms, launches = md.mdn_profile(nw.ctx, 0)
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t_max = total_ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    value = world * args.steps / (t_max * 1e-3)
+
+    # end to end: whole solves from pinned host memory through the API
+    x0_host = torch.from_numpy(x0).pin_memory()
+    x_host = torch.empty_like(x0_host).pin_memory()
+    hist = None
+    e2e_ms = []
+    for rep in range(args.e2e_solves + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        x0_dev.copy_(x0_host, non_blocking=True)
+        nw.set_series(x0_dev)
+        st, done, hist = md.mdn_newton(nw.ctx, cfg.steps, 0.0)
+        x_out = nw.series()
+        x_host.copy_(x_out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep > 0:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = world * cfg.steps / (statistics.median(e2e_ms) * 1e-3)
+    nbytes = x0.nbytes
+
+    # roofline of the phase with the largest share of device time
+    counts = F.step_counts(s.monomial_sizes(), s.n, s.D, s.K, s.C)
+    steps_timed = args.steps
+    per_phase_ops = {"evaluate": counts["evaluate"]["fp64_ops"], "qr": counts["solve"]["qr_fp64_ops"],
+                     "forward": counts["solve"]["forward_fp64_ops"]}
+    share = {p: float(ms) for p, ms in zip(md.PHASES, phase_ms)}
+    dom = max(per_phase_ops, key=lambda p: share[p])
+    dom_launch_ms = share[dom] / steps_timed
+    achieved = per_phase_ops[dom] / (dom_launch_ms * 1e-3)
+    eval_ms = share["evaluate"] / steps_timed
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(cfg), "data": "synthetic",
+        "config": config_dict(cfg, args),
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": FP64_PEAK_OPS / 1e12,
+                     "unit": "FP64 Tops/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 1.684 FP64 lanes/clk/SM (measured) x 2070 MHz",
+                     "ops_per_launch": per_phase_ops[dom]},
+        "phases_ms_per_step": {p: share[p] / steps_timed for p in md.PHASES},
+        "evaluate_roofline_frac": (per_phase_ops["evaluate"] / (eval_ms * 1e-3)) / FP64_PEAK_OPS if eval_ms > 0 else None,
+        "step_fp64_ops": counts["fp64_ops"], "step_paper_flops": counts["paper_flops"],
+        "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": nbytes / cfg.steps,
+                "d2h_bytes_per_step": (nbytes + 24 * cfg.steps) / cfg.steps,
+                "solve_ms": statistics.median(e2e_ms)},
+        "gpu_launches": int(np.sum(launches)),
+        "clocks": clk,
+        "check": {"max_leading_limb_error_vs_plant": diff, "final_norm_f": float(hist[-1, 0]) if hist is not None else None},
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, cores = oracle_sample(cfg, args.cpu_sample_steps)
+        line["cpu_baseline"] = {"value": args.cpu_sample_steps / dt, "unit": "steps/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{args.cpu_sample_steps} oracle Newton steps from the start series"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    nw.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    cfg = wl.CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

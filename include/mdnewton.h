@@ -1,0 +1,168 @@
+/*
+ * mdnewton.h -- C-ABI of libmdnewton: Newton's method on truncated power
+ * series in multiple double arithmetic on one GB300 GPU (sm_103a).
+ *
+ * Method (J. Verschelde, "GPU Accelerated Newton for Taylor Series Solutions
+ * of Polynomial Homotopies in Multiple Double Precision", arXiv 2301.12659):
+ * one Newton step evaluates and differentiates a polynomial system f at a
+ * vector of truncated power series x(t) (Section 5.1: forward, backward and
+ * cross products of every monomial), then solves the block lower triangular
+ * Toeplitz system A(t) dx(t) = -f(x(t)) mod t^(d+1) (Section 2, Eq.
+ * (eqToeplitz)) with a Householder QR of the leading matrix A0 (Section 5.3)
+ * and forward substitution dx_k = A0^{-1} (b_k - sum_{j>=1} A_j dx_{k-j}),
+ * and updates x := x + dx.  The calls follow the problem statement of
+ * Section 2 (input: the system with series coefficients, the leading
+ * coefficients of the start series, the number of iterations; output: the
+ * series and the residuals).
+ *
+ * Numbers.  A multiple double (md) with K limbs (K = 2 double double, 4 quad
+ * double, 8 octo double) is an unevaluated sum of K nonoverlapping doubles
+ * (Section 1.2).  Complex data (C = 2) have a real and an imaginary md part.
+ *
+ * Layout.  Every md array is structure of arrays, one array per limb and part
+ * (Section 1.2): an array of N md values is float64 [K][C][N], element
+ * (limb l, part c, index i) at offset (l*C + c)*N + i.  Concretely
+ *   series    x, f, dx   [K][C][n][d+1]    coefficient k of variable v at i = v*(d+1) + k
+ *   coeffs    coeff      [K][C][M][d+1]    coefficient k of monomial m at i = m*(d+1) + k
+ *   Jacobian  A          [K][C][d+1][n][n] entry (j, i, v) at i' = (j*n + i)*n + v
+ * where A_j[i][v] = [t^j] d f_i / d x_v.
+ *
+ * System.  Equation i is f_i = sum_{m : eq[m] = i} coeff_m(t) prod_{p} x_{var_idx[p]}(t)
+ * + cst_i(t), the product over p = var_ptr[m] .. var_ptr[m+1]-1 (a repeated
+ * variable index is a power).  Linear terms such as a diagonal 64 x_i are
+ * monomials with one variable and a constant coefficient series.
+ *
+ * Ownership.  The library allocates no device memory.  The caller allocates
+ * every device buffer, including the workspace sized by
+ * mdn_workspace_bytes(); the library borrows the pointers until the next
+ * mdn_load_system() or mdn_destroy().  All device work is enqueued on the
+ * stream given to mdn_load_system().  Host pointers are only read during the
+ * call.
+ *
+ * Errors.  Every call returns an mdn_status and never throws.  Device-side
+ * conditions (zero pivot in the QR of A0, non-finite values, a bounded wait
+ * that timed out) are collected in a status word and reported by the call
+ * that synchronises (mdn_newton, mdn_solve, mdn_status_word).
+ * mdn_last_error() gives a message for the last failure on a context.
+ */
+#ifndef MDNEWTON_H
+#define MDNEWTON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mdn_ctx mdn_ctx;
+
+typedef enum {
+  MDN_OK = 0,
+  MDN_EINVAL = 1,          /* invalid argument or size */
+  MDN_ECUDA = 2,           /* a CUDA runtime call failed */
+  MDN_ESINGULAR = 3,       /* A0 has a zero pivot (Householder norm 0) */
+  MDN_ENONFINITE = 4,      /* a non-finite value appeared in the series */
+  MDN_ENOTCONVERGED = 5,   /* tolerance not met within max_steps; x readable */
+  MDN_ETIMEOUT = 6,        /* a bounded device wait gave up */
+  MDN_ESTATE = 7,          /* call out of order (no system or series loaded) */
+  MDN_EWORKSPACE = 8       /* workspace smaller than mdn_workspace_bytes() */
+} mdn_status;
+
+/* Most Newton steps one mdn_newton() call may run (size of the device history). */
+#define MDN_MAX_STEPS 64
+/* Largest truncation degree supported (d+1 <= 64 coefficients). */
+#define MDN_MAX_DEGREE 63
+
+/* Create a context for K limbs (2, 4 or 8; 1 runs plain doubles), real
+ * (is_complex = 0) or complex (1) data, n >= 1 equations and unknowns and
+ * truncation degree 0 <= degree <= MDN_MAX_DEGREE.  *out receives the context
+ * (host memory); MDN_EINVAL on bad sizes, MDN_ECUDA without a usable GPU. */
+mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degree);
+
+/* Bytes of device workspace mdn_load_system() needs for a system of
+ * n_monomials monomials with CSR offsets var_ptr (host, n_monomials+1
+ * entries).  Returns 0 on invalid arguments. */
+size_t mdn_workspace_bytes(const mdn_ctx* ctx, int n_monomials, const int32_t* var_ptr);
+
+/* Load the system (Section 2 problem statement: f with power series
+ * coefficients and the truncation degree d).
+ *   eq_of_monomial [M]    host, equation of each monomial (0 <= eq < n)
+ *   var_ptr       [M+1]   host, CSR offsets into var_idx, var_ptr[0] = 0,
+ *                         at least one variable per monomial
+ *   var_idx       [nnz]   host, variable indices (0 <= v < n)
+ *   coeff         device, [K][C][M][d+1]
+ *   const_term    device, [K][C][n][d+1]
+ *   workspace     device, >= mdn_workspace_bytes() bytes, 256-byte aligned
+ *   cuda_stream   a cudaStream_t (NULL = legacy default stream)
+ * The call copies the structure into the workspace and synchronises the
+ * stream once.  coeff and const_term are read by later calls, not copied. */
+mdn_status mdn_load_system(mdn_ctx* ctx, int n_monomials, const int32_t* eq_of_monomial,
+                           const int32_t* var_ptr, const int32_t* var_idx, const double* coeff,
+                           const double* const_term, void* workspace, size_t ws_bytes,
+                           void* cuda_stream);
+
+/* Set the current series x(t) (device [K][C][n][d+1], copied on the stream). */
+mdn_status mdn_set_series(mdn_ctx* ctx, const double* x);
+
+/* Run Newton steps (Section 2 pseudo code) from the current series.  With
+ * tol <= 0 exactly max_steps steps run with one synchronisation at the end;
+ * with tol > 0 the loop stops after the first step whose ||dx||_1 <= tol
+ * (MDN_ENOTCONVERGED if none).  steps_done (host, may be NULL) receives the
+ * number of steps run; res_hist (host, may be NULL) receives per step the
+ * three doubles ||f(x)||_1 before the update, the residual
+ * ||b - A dx||_1 of the linear solve (b = -f) and ||dx||_1, each the 1-norm
+ * of the leading doubles of the md entries.  1 <= max_steps <= MDN_MAX_STEPS. */
+mdn_status mdn_newton(mdn_ctx* ctx, int max_steps, double tol, int* steps_done, double* res_hist);
+
+/* Copy the current series to x_out (device [K][C][n][d+1]). */
+mdn_status mdn_get_series(const mdn_ctx* ctx, double* x_out);
+
+/* Evaluate f at the current series into f_out (device [K][C][n][d+1]). */
+mdn_status mdn_get_residual(mdn_ctx* ctx, double* f_out);
+
+/* Evaluation and differentiation only (Section 5.1): f(x) into f_out and, when
+ * A_out is not NULL, the Jacobian series into A_out (device
+ * [K][C][d+1][n][n]).  x is a device series [K][C][n][d+1]. */
+mdn_status mdn_evaluate(mdn_ctx* ctx, const double* x, double* f_out, double* A_out);
+
+/* Linear solve only (Section 2, Eq. (eqToeplitz), with the Householder QR of
+ * A0 of Section 5.3): dx with sum_{j<=k} A_j dx_{k-j} = b_k for k = 0..d.
+ * A device [K][C][d+1][n][n], b and dx device [K][C][n][d+1].  Synchronises;
+ * MDN_ESINGULAR for a zero pivot. */
+mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx);
+
+/* Phases of a Newton step for mdn_profile(), after the kernel types of the
+ * paper's Table 3 (Section 6.2): evaluation and differentiation
+ * ("convolutions"), assembly of f and A, Householder QR with Q^H and back
+ * substitution forming A0^{-1} ("qr", "qhb", "bs"), forward substitution
+ * with the right hand side updates and residuals ("updates", "residuals"),
+ * and the update of x with the norms of the step. */
+#define MDN_NUM_PHASES 5
+#define MDN_PHASE_EVALUATE 0
+#define MDN_PHASE_ASSEMBLE 1
+#define MDN_PHASE_QR 2
+#define MDN_PHASE_FORWARD 3
+#define MDN_PHASE_UPDATE 4
+
+/* Device timers per phase.  enable = 1 clears the accumulators and starts
+ * recording a CUDA event pair around every phase of later calls (on the
+ * context's stream); enable = 0 stops recording, synchronises and writes the
+ * accumulated milliseconds (ms_out) and kernel launch counts (launches_out)
+ * per phase into host arrays of MDN_NUM_PHASES entries (either may be NULL). */
+mdn_status mdn_profile(mdn_ctx* ctx, int enable, double* ms_out, int64_t* launches_out);
+
+/* Synchronise the context's stream and return the device status as an
+ * mdn_status (MDN_OK when no device condition was raised). */
+mdn_status mdn_status_word(mdn_ctx* ctx);
+
+/* Message of the last failure on ctx (never NULL; "" when none). */
+const char* mdn_last_error(const mdn_ctx* ctx);
+
+/* Release the context (host memory only; device buffers stay the caller's). */
+void mdn_destroy(mdn_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDNEWTON_H */

@@ -414,7 +414,7 @@ static int evaluate(const sys_t *S, const mdc *X, mdc *F, mdc *A) {
             mdc *v = &val[(size_t)q * D];
             memcpy(v, &S->coeff[(size_t)m * D], sizeof(mdc) * D);
             for (int p = 0; p < k; ++p) series_mul(v, &X[(size_t)S->vidx[p0 + p] * D], v, d, K, C);
-            for (int jj = 0; jj < k; ++jj, ++s) {
+            for (int jj = 0; A && jj < k; ++jj, ++s) {
                 mdc *g = &par[(size_t)s * D];
                 slot_var[s] = S->vidx[p0 + jj];
                 memcpy(g, &S->coeff[(size_t)m * D], sizeof(mdc) * D);

@@ -1,0 +1,727 @@
+// api.cu -- host runtime of libmdnewton: the C-ABI of include/mdnewton.h.
+//
+// The runtime owns no device memory.  mdn_load_system() lays out the
+// caller's workspace, builds on the host the tables the kernels read
+// (monomial order for the dynamic work queue, the product schedule of every
+// monomial size, the gather lists of f and A) and copies them in.  A Newton
+// step (Section 2) is then a fixed sequence of launches on the caller's
+// stream: evaluation and differentiation, assembly, QR of A0 and its
+// inverse, d+1 forward substitution stages, update and norms.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mdnewton.h"
+#include "params.h"
+
+namespace mdn {
+const KernelTable* kernels_k1_c1();
+const KernelTable* kernels_k2_c1();
+const KernelTable* kernels_k2_c2();
+const KernelTable* kernels_k4_c1();
+const KernelTable* kernels_k4_c2();
+const KernelTable* kernels_k8_c1();
+const KernelTable* kernels_k8_c2();
+
+const KernelTable* kernels_for(int K, int C) {
+  if (K == 1 && C == 1) return kernels_k1_c1();
+  if (K == 2 && C == 1) return kernels_k2_c1();
+  if (K == 2 && C == 2) return kernels_k2_c2();
+  if (K == 4 && C == 1) return kernels_k4_c1();
+  if (K == 4 && C == 2) return kernels_k4_c2();
+  if (K == 8 && C == 1) return kernels_k8_c1();
+  if (K == 8 && C == 2) return kernels_k8_c2();
+  return nullptr;
+}
+
+// Bounded waits of the dataflow kernels: two seconds of wall time at most.
+constexpr long long SPIN_LIMIT = 2000000000LL;
+
+__global__ void bump_kernel(unsigned* epoch) { *epoch += 1u; }
+
+// Deterministic sums of three magnitude arrays into hist[0..2] (one block,
+// fixed order: strided partial sums, then a tree).
+__global__ void norms_kernel(NormParams p) {
+  __shared__ double sh[3][1024];
+  const int t = threadIdx.x;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (long long i = t; i < p.count; i += blockDim.x) {
+    s0 += p.fabs[i];
+    s1 += p.resabs[i];
+    s2 += p.dxabs[i];
+  }
+  sh[0][t] = s0;
+  sh[1][t] = s1;
+  sh[2][t] = s2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (t < w) {
+      sh[0][t] += sh[0][t + w];
+      sh[1][t] += sh[1][t + w];
+      sh[2][t] += sh[2][t + w];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    p.hist[0] = sh[0][0];
+    p.hist[1] = sh[1][0];
+    p.hist[2] = sh[2][0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Product schedule of one monomial with k variables (Section 5.1): forward
+// products F_j = F_{j-1} x_j (F_0 = c, F_k = value), backward products
+// B_j = B_{j-1} x_{k-j+1} (B_1 = x_k) and cross products d_j = F_{j-1} B_{k-j}
+// (d_1 = c B_{k-1}, d_k = F_{k-1}): 3k-3 truncated products for k >= 2.
+// Tasks are list-scheduled in waves of at most G products that run at once
+// in one warp (G groups of lanes), longest remaining chain first.
+// ---------------------------------------------------------------------------
+static int code(int kind, int idx) { return (kind << 16) | idx; }
+
+static void build_schedule(int k, int G, std::vector<int4>& waves_out, int& nwaves) {
+  struct Task {
+    int type, dst, a, b;
+    std::vector<int> deps;
+    int prio;
+  };
+  std::vector<Task> T;
+  auto fcode = [&](int j) {
+    if (j == 0) return code(SLOT_C, 0);
+    if (j == k) return code(SLOT_V, 0);
+    if (j == k - 1) return code(SLOT_P, k - 1);
+    return code(SLOT_F, j);
+  };
+  auto bcode = [&](int j) { return j == 1 ? code(SLOT_X, k - 1) : code(SLOT_B, j); };
+  if (k == 1) {
+    T.push_back({OP_PRODUCT, code(SLOT_V, 0), code(SLOT_C, 0), code(SLOT_X, 0), {}, 0});
+    T.push_back({OP_COPY, code(SLOT_P, 0), code(SLOT_C, 0), 0, {}, 0});
+  } else {
+    std::vector<int> fidx(k + 1, -1), bidx(k + 1, -1);
+    for (int j = 1; j <= k; ++j) {
+      Task t{OP_PRODUCT, fcode(j), fcode(j - 1), code(SLOT_X, j - 1), {}, 0};
+      if (j >= 2) t.deps.push_back(fidx[j - 1]);
+      fidx[j] = (int)T.size();
+      T.push_back(t);
+    }
+    for (int j = 2; j <= k - 1; ++j) {
+      Task t{OP_PRODUCT, bcode(j), bcode(j - 1), code(SLOT_X, k - j), {}, 0};
+      if (j >= 3) t.deps.push_back(bidx[j - 1]);
+      bidx[j] = (int)T.size();
+      T.push_back(t);
+    }
+    for (int p = 0; p <= k - 2; ++p) {
+      const int bj = k - 1 - p;
+      Task t{OP_PRODUCT, code(SLOT_P, p), fcode(p), bcode(bj), {}, 0};
+      if (p >= 1) t.deps.push_back(fidx[p]);
+      if (bj >= 2) t.deps.push_back(bidx[bj]);
+      T.push_back(t);
+    }
+  }
+  // priority: length of the longest chain of dependents (tasks only depend on
+  // earlier tasks, so a reverse sweep suffices)
+  const int nt = (int)T.size();
+  std::vector<int> longest(nt, 1);
+  for (int i = nt - 1; i >= 0; --i)
+    for (int d : T[i].deps) longest[d] = std::max(longest[d], longest[i] + 1);
+  std::vector<int> done(nt, 0);
+  int ndone = 0;
+  nwaves = 0;
+  while (ndone < nt) {
+    std::vector<int> ready;
+    for (int i = 0; i < nt; ++i) {
+      if (done[i]) continue;
+      bool ok = true;
+      for (int d : T[i].deps) ok = ok && done[d] == 1;
+      if (ok) ready.push_back(i);
+    }
+    std::stable_sort(ready.begin(), ready.end(), [&](int a, int b) { return longest[a] > longest[b]; });
+    const int take = std::min<int>(G, (int)ready.size());
+    for (int g = 0; g < G; ++g) {
+      if (g < take) {
+        const Task& t = T[ready[g]];
+        waves_out.push_back(make_int4(t.type, t.dst, t.a, t.b));
+      } else {
+        waves_out.push_back(make_int4(OP_NONE, 0, 0, 0));
+      }
+    }
+    for (int g = 0; g < take; ++g) done[ready[g]] = 2;  // finished at the end of this wave
+    for (int i = 0; i < nt; ++i)
+      if (done[i] == 2) {
+        done[i] = 1;
+        ++ndone;
+      }
+    ++nwaves;
+  }
+}
+
+}  // namespace mdn
+
+using namespace mdn;
+
+struct Layout {
+  size_t total = 0;
+  size_t o_order, o_mono_k, o_mono_vp, o_mono_sbase, o_vidx, o_sched, o_sched_off, o_sched_nw, o_eq_ptr,
+      o_eq_mon, o_pair_ptr, o_pair_slot, o_counter, o_status, o_flags, o_epoch;
+  size_t o_x, o_f, o_dx, o_r, o_out, o_scratch, o_A, o_Rm, o_Vm, o_Y, o_W, o_tau, o_rinv, o_fabs, o_dxabs,
+      o_resabs, o_hist;
+};
+
+struct mdn_ctx {
+  int K, C, n, d, D;
+  const KernelTable* kt = nullptr;
+  int num_sms = 0, ed_grid = 0, Wtot = 0;
+  int P = 1, G = 1;
+  // system (host tables)
+  int M = 0, nnz = 0, S = 0, kmax = 1, Smax = 1;
+  std::vector<int> order, mono_k, mono_vp, mono_sbase, vidx, sched_off, sched_nw, eq_ptr, eq_mon, pair_ptr,
+      pair_slot;
+  std::vector<int4> sched;
+  bool loaded = false, has_series = false;
+  const double* coeff = nullptr;
+  const double* cst = nullptr;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  Layout L;
+  std::string err;
+  // phase timers (mdn_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_rec;
+  int open_phase = -1;
+  cudaEvent_t open_ev = nullptr;
+  long long launches[MDN_NUM_PHASES] = {0, 0, 0, 0, 0};
+  template <class T>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(ws + off);
+  }
+};
+
+static mdn_status fail(const mdn_ctx* c, mdn_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    const_cast<mdn_ctx*>(c)->err = buf;
+  }
+  return s;
+}
+
+#define CU(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return fail(ctx, MDN_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static cudaEvent_t prof_event(mdn_ctx* ctx) {
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    ctx->ev_pool.push_back(e);
+  }
+  return ctx->ev_pool[ctx->ev_used++];
+}
+// Open a phase: record its start event when the timers run.
+static void ph_begin(mdn_ctx* ctx, int phase) {
+  if (!ctx->prof) return;
+  cudaEvent_t e = prof_event(ctx);
+  if (!e) return;
+  cudaEventRecord(e, ctx->stream);
+  ctx->open_phase = phase;
+  ctx->open_ev = e;
+}
+static void ph_end(mdn_ctx* ctx, int phase, int launches) {
+  ctx->launches[phase] += launches;
+  if (!ctx->prof || ctx->open_phase != phase) return;
+  cudaEvent_t e = prof_event(ctx);
+  if (!e) return;
+  cudaEventRecord(e, ctx->stream);
+  ctx->prof_rec.push_back({phase, {ctx->open_ev, e}});
+  ctx->open_phase = -1;
+}
+
+// Tables that depend only on the structure of the system.
+static mdn_status build_tables(mdn_ctx* ctx, int M, const int32_t* eq, const int32_t* vptr, const int32_t* vidx) {
+  const int n = ctx->n;
+  if (M < 1 || !vptr) return fail(ctx, MDN_EINVAL, "need at least one monomial and var_ptr");
+  if (vptr[0] != 0) return fail(ctx, MDN_EINVAL, "var_ptr[0] must be 0");
+  int kmax = 1;
+  for (int m = 0; m < M; ++m) {
+    const int k = vptr[m + 1] - vptr[m];
+    if (k < 1) return fail(ctx, MDN_EINVAL, "monomial %d has no variable", m);
+    if (k > 4096) return fail(ctx, MDN_EINVAL, "monomial %d has %d variables (max 4096)", m, k);
+    kmax = std::max(kmax, k);
+  }
+  ctx->M = M;
+  ctx->nnz = vptr[M];
+  ctx->kmax = kmax;
+  ctx->Smax = std::max(1, 2 * kmax - 4);
+  ctx->mono_k.assign(M, 0);
+  ctx->mono_vp.assign(M, 0);
+  ctx->mono_sbase.assign(M, 0);
+  int S = 0;
+  for (int m = 0; m < M; ++m) {
+    ctx->mono_k[m] = vptr[m + 1] - vptr[m];
+    ctx->mono_vp[m] = vptr[m];
+    ctx->mono_sbase[m] = S;
+    S += ctx->mono_k[m] + 1;
+  }
+  ctx->S = S;
+  // work queue order: most expensive monomials first (longest processing time)
+  ctx->order.resize(M);
+  for (int m = 0; m < M; ++m) ctx->order[m] = m;
+  std::stable_sort(ctx->order.begin(), ctx->order.end(),
+                   [&](int a, int b) { return ctx->mono_k[a] > ctx->mono_k[b]; });
+  // schedules for every size 1..kmax
+  ctx->sched.clear();
+  ctx->sched_off.assign(kmax + 1, 0);
+  ctx->sched_nw.assign(kmax + 1, 0);
+  for (int k = 1; k <= kmax; ++k) {
+    ctx->sched_off[k] = (int)ctx->sched.size();
+    int nw = 0;
+    build_schedule(k, ctx->G, ctx->sched, nw);
+    ctx->sched_nw[k] = nw;
+  }
+  if (eq && vidx) {
+    for (int m = 0; m < M; ++m)
+      if (eq[m] < 0 || eq[m] >= n) return fail(ctx, MDN_EINVAL, "eq_of_monomial[%d] = %d out of range", m, eq[m]);
+    for (int q = 0; q < ctx->nnz; ++q)
+      if (vidx[q] < 0 || vidx[q] >= n) return fail(ctx, MDN_EINVAL, "var_idx[%d] = %d out of range", q, vidx[q]);
+    ctx->vidx.assign(vidx, vidx + ctx->nnz);
+    // equation lists (monomials in index order)
+    ctx->eq_ptr.assign(n + 1, 0);
+    for (int m = 0; m < M; ++m) ctx->eq_ptr[eq[m] + 1]++;
+    for (int i = 0; i < n; ++i) ctx->eq_ptr[i + 1] += ctx->eq_ptr[i];
+    ctx->eq_mon.assign(M, 0);
+    {
+      std::vector<int> fill(ctx->eq_ptr.begin(), ctx->eq_ptr.end() - 1);
+      for (int m = 0; m < M; ++m) ctx->eq_mon[fill[eq[m]]++] = m;
+    }
+    // (row, variable) gather lists of the Jacobian: slot of every occurrence
+    const long long nn = (long long)n * n;
+    ctx->pair_ptr.assign(nn + 1, 0);
+    for (int m = 0; m < M; ++m)
+      for (int q = vptr[m]; q < vptr[m + 1]; ++q) ctx->pair_ptr[(long long)eq[m] * n + vidx[q] + 1]++;
+    for (long long t = 0; t < nn; ++t) ctx->pair_ptr[t + 1] += ctx->pair_ptr[t];
+    ctx->pair_slot.assign(ctx->nnz, 0);
+    {
+      std::vector<int> fill(ctx->pair_ptr.begin(), ctx->pair_ptr.end() - 1);
+      for (int i = 0; i < n; ++i)
+        for (int e = ctx->eq_ptr[i]; e < ctx->eq_ptr[i + 1]; ++e) {
+          const int m = ctx->eq_mon[e];
+          for (int q = vptr[m]; q < vptr[m + 1]; ++q)
+            ctx->pair_slot[fill[(long long)i * n + vidx[q]]++] = ctx->mono_sbase[m] + 1 + (q - vptr[m]);
+        }
+    }
+  }
+  return MDN_OK;
+}
+
+static void compute_layout(mdn_ctx* ctx) {
+  Layout& L = ctx->L;
+  const size_t KC = (size_t)ctx->K * ctx->C;
+  const size_t n = ctx->n, D = ctx->D, M = ctx->M;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + std::max<size_t>(bytes, 8));
+    return at;
+  };
+  L.o_order = take(4 * M);
+  L.o_mono_k = take(4 * M);
+  L.o_mono_vp = take(4 * M);
+  L.o_mono_sbase = take(4 * M);
+  L.o_vidx = take(4 * (size_t)ctx->nnz);
+  L.o_sched = take(sizeof(int4) * ctx->sched.size());
+  L.o_sched_off = take(4 * ctx->sched_off.size());
+  L.o_sched_nw = take(4 * ctx->sched_nw.size());
+  L.o_eq_ptr = take(4 * (n + 1));
+  L.o_eq_mon = take(4 * M);
+  L.o_pair_ptr = take(4 * (n * n + 1));
+  L.o_pair_slot = take(4 * (size_t)ctx->nnz);
+  L.o_counter = take(4);
+  L.o_status = take(4);
+  L.o_flags = take(4 * 2 * n);
+  L.o_epoch = take(4);
+  const size_t ser = 8 * KC * n * D;
+  L.o_x = take(ser);
+  L.o_f = take(ser);
+  L.o_dx = take(ser);
+  L.o_r = take(ser);
+  L.o_out = take(8 * KC * (size_t)ctx->S * D);
+  L.o_scratch = take(8 * KC * (size_t)ctx->Wtot * ctx->Smax * D);
+  L.o_A = take(8 * KC * D * n * n);
+  L.o_Rm = take(8 * KC * n * n);
+  L.o_Vm = take(8 * KC * n * n);
+  L.o_Y = take(8 * KC * n * n);
+  L.o_W = take(8 * KC * n * n);
+  L.o_tau = take(8 * (size_t)ctx->K * n);
+  L.o_rinv = take(8 * KC * n);
+  L.o_fabs = take(8 * n * D);
+  L.o_dxabs = take(8 * n * D);
+  L.o_resabs = take(8 * n * D);
+  L.o_hist = take(8 * 3 * MDN_MAX_STEPS);
+  L.total = o;
+}
+
+extern "C" {
+
+mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degree) {
+  if (!out) return MDN_EINVAL;
+  *out = nullptr;
+  const int C = is_complex ? 2 : 1;
+  const KernelTable* kt = kernels_for(limbs, C);
+  if (!kt || n < 1 || n > 4096 || degree < 0 || degree > MDN_MAX_DEGREE) return MDN_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MDN_ECUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MDN_ECUDA;
+  mdn_ctx* ctx = new (std::nothrow) mdn_ctx();
+  if (!ctx) return MDN_EINVAL;
+  ctx->K = limbs;
+  ctx->C = C;
+  ctx->n = n;
+  ctx->d = degree;
+  ctx->D = degree + 1;
+  ctx->kt = kt;
+  ctx->num_sms = sms;
+  ctx->P = (ctx->D + 1) / 2;  // lanes per product: coefficient pairs (k, D-1-k)
+  ctx->G = 32 / ctx->P;       // products in flight per warp
+  const int bps = std::max(1, kt->ed_blocks_per_sm());
+  ctx->ed_grid = sms * bps;
+  *out = ctx;
+  return MDN_OK;
+}
+
+size_t mdn_workspace_bytes(const mdn_ctx* cctx, int n_monomials, const int32_t* var_ptr) {
+  if (!cctx || !var_ptr || n_monomials < 1) return 0;
+  mdn_ctx tmp = *cctx;
+  tmp.err.clear();
+  if (build_tables(&tmp, n_monomials, nullptr, var_ptr, nullptr) != MDN_OK) return 0;
+  tmp.nnz = var_ptr[n_monomials];
+  tmp.Wtot = std::min(tmp.ed_grid * (ED_THREADS / 32), n_monomials);
+  compute_layout(&tmp);
+  return tmp.L.total;
+}
+
+mdn_status mdn_load_system(mdn_ctx* ctx, int M, const int32_t* eq, const int32_t* vptr, const int32_t* vidx,
+                           const double* coeff, const double* cst, void* workspace, size_t ws_bytes,
+                           void* cuda_stream) {
+  if (!ctx) return MDN_EINVAL;
+  ctx->loaded = false;
+  ctx->has_series = false;
+  if (!eq || !vptr || !vidx || !coeff || !cst || !workspace)
+    return fail(ctx, MDN_EINVAL, "null pointer argument");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(ctx, MDN_EINVAL, "workspace not 256-byte aligned");
+  mdn_status s = build_tables(ctx, M, eq, vptr, vidx);
+  if (s != MDN_OK) return s;
+  // more warps than monomials would only idle
+  ctx->Wtot = std::min(ctx->ed_grid * (ED_THREADS / 32), M);
+  compute_layout(ctx);
+  if (ws_bytes < ctx->L.total)
+    return fail(ctx, MDN_EWORKSPACE, "workspace has %zu bytes, needs %zu", ws_bytes, ctx->L.total);
+  ctx->ws = static_cast<char*>(workspace);
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->coeff = coeff;
+  ctx->cst = cst;
+  const Layout& L = ctx->L;
+  cudaStream_t st = ctx->stream;
+  auto put = [&](size_t off, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(ctx->ws + off, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  };
+  CU(put(L.o_order, ctx->order.data(), 4 * ctx->order.size()));
+  CU(put(L.o_mono_k, ctx->mono_k.data(), 4 * ctx->mono_k.size()));
+  CU(put(L.o_mono_vp, ctx->mono_vp.data(), 4 * ctx->mono_vp.size()));
+  CU(put(L.o_mono_sbase, ctx->mono_sbase.data(), 4 * ctx->mono_sbase.size()));
+  CU(put(L.o_vidx, ctx->vidx.data(), 4 * ctx->vidx.size()));
+  CU(put(L.o_sched, ctx->sched.data(), sizeof(int4) * ctx->sched.size()));
+  CU(put(L.o_sched_off, ctx->sched_off.data(), 4 * ctx->sched_off.size()));
+  CU(put(L.o_sched_nw, ctx->sched_nw.data(), 4 * ctx->sched_nw.size()));
+  CU(put(L.o_eq_ptr, ctx->eq_ptr.data(), 4 * ctx->eq_ptr.size()));
+  CU(put(L.o_eq_mon, ctx->eq_mon.data(), 4 * ctx->eq_mon.size()));
+  CU(put(L.o_pair_ptr, ctx->pair_ptr.data(), 4 * ctx->pair_ptr.size()));
+  CU(put(L.o_pair_slot, ctx->pair_slot.data(), 4 * ctx->pair_slot.size()));
+  CU(cudaMemsetAsync(ctx->ws + L.o_counter, 0, 4, st));
+  CU(cudaMemsetAsync(ctx->ws + L.o_status, 0, 4, st));
+  CU(cudaMemsetAsync(ctx->ws + L.o_flags, 0, 4 * 2 * (size_t)ctx->n, st));
+  CU(cudaMemsetAsync(ctx->ws + L.o_epoch, 0, 4, st));
+  CU(cudaMemsetAsync(ctx->ws + L.o_dx, 0, 8 * (size_t)ctx->K * ctx->C * ctx->n * ctx->D, st));
+  CU(cudaStreamSynchronize(st));  // host tables may be reused after return
+  ctx->loaded = true;
+  ctx->err.clear();
+  return MDN_OK;
+}
+
+mdn_status mdn_set_series(mdn_ctx* ctx, const double* x) {
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
+  if (!x) return fail(ctx, MDN_EINVAL, "null series");
+  CU(cudaMemcpyAsync(ctx->at<double>(ctx->L.o_x), x, 8 * (size_t)ctx->K * ctx->C * ctx->n * ctx->D,
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->has_series = true;
+  return MDN_OK;
+}
+
+mdn_status mdn_get_series(const mdn_ctx* cctx, double* x_out) {
+  mdn_ctx* ctx = const_cast<mdn_ctx*>(cctx);
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->has_series) return fail(ctx, MDN_ESTATE, "no series set");
+  if (!x_out) return fail(ctx, MDN_EINVAL, "null output");
+  CU(cudaMemcpyAsync(x_out, ctx->at<double>(ctx->L.o_x), 8 * (size_t)ctx->K * ctx->C * ctx->n * ctx->D,
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  return MDN_OK;
+}
+
+// ---- launch sequences -------------------------------------------------------
+
+static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double* A) {
+  const Layout& L = ctx->L;
+  const long long D = ctx->D, n = ctx->n;
+  EdParams e{};
+  e.n = ctx->n;
+  e.D = ctx->D;
+  e.M = ctx->M;
+  e.P = ctx->P;
+  e.G = ctx->G;
+  e.kmax = ctx->kmax;
+  e.Smax = ctx->Smax;
+  e.Wtot = ctx->Wtot;
+  e.x = x;
+  e.Nx = n * D;
+  e.coeff = ctx->coeff;
+  e.Nc = (long long)ctx->M * D;
+  e.out = ctx->at<double>(L.o_out);
+  e.No = (long long)ctx->S * D;
+  e.scratch = ctx->at<double>(L.o_scratch);
+  e.Ns = (long long)ctx->Wtot * ctx->Smax * D;
+  e.order = ctx->at<int>(L.o_order);
+  e.mono_k = ctx->at<int>(L.o_mono_k);
+  e.mono_vp = ctx->at<int>(L.o_mono_vp);
+  e.mono_sbase = ctx->at<int>(L.o_mono_sbase);
+  e.vidx = ctx->at<int>(L.o_vidx);
+  e.sched = ctx->at<int4>(L.o_sched);
+  e.sched_off = ctx->at<int>(L.o_sched_off);
+  e.sched_nw = ctx->at<int>(L.o_sched_nw);
+  e.counter = ctx->at<int>(L.o_counter);
+  ph_begin(ctx, MDN_PHASE_EVALUATE);
+  CU(cudaMemsetAsync(e.counter, 0, 4, ctx->stream));
+  const int grid = (ctx->Wtot + (ED_THREADS / 32) - 1) / (ED_THREADS / 32);
+  CU(ctx->kt->ed(e, grid, ctx->stream));
+  ph_end(ctx, MDN_PHASE_EVALUATE, 1);
+  AsmParams a{};
+  a.n = ctx->n;
+  a.D = ctx->D;
+  a.out = e.out;
+  a.No = e.No;
+  a.cst = ctx->cst;
+  a.f = f;
+  a.Nf = n * D;
+  a.A = A;
+  a.NA = D * n * n;
+  a.eq_ptr = ctx->at<int>(L.o_eq_ptr);
+  a.eq_mon = ctx->at<int>(L.o_eq_mon);
+  a.mono_sbase = e.mono_sbase;
+  a.pair_ptr = ctx->at<int>(L.o_pair_ptr);
+  a.pair_slot = ctx->at<int>(L.o_pair_slot);
+  ph_begin(ctx, MDN_PHASE_ASSEMBLE);
+  CU(ctx->kt->assemble(a, A != nullptr, ctx->stream));
+  ph_end(ctx, MDN_PHASE_ASSEMBLE, A != nullptr ? 2 : 1);
+  return MDN_OK;
+}
+
+// QR of A0 (the j = 0 slice of A), W = A0^{-1}, then the forward substitution
+// for dx with right hand side sgn * rhs.
+static mdn_status run_solve(mdn_ctx* ctx, const double* A, const double* rhs, int sgn, double* dx) {
+  const Layout& L = ctx->L;
+  const long long D = ctx->D, n = ctx->n;
+  ph_begin(ctx, MDN_PHASE_QR);
+  bump_kernel<<<1, 1, 0, ctx->stream>>>(ctx->at<unsigned>(L.o_epoch));
+  CU(cudaGetLastError());
+  QrParams q{};
+  q.n = ctx->n;
+  q.nA = (ctx->n + (QR_THREADS / 32) - 1) / (QR_THREADS / 32);
+  q.A0 = A;
+  q.NA = D * n * n;
+  q.Nnn = n * n;
+  q.Rm = ctx->at<double>(L.o_Rm);
+  q.Vm = ctx->at<double>(L.o_Vm);
+  q.Y = ctx->at<double>(L.o_Y);
+  q.W = ctx->at<double>(L.o_W);
+  q.tau = ctx->at<double>(L.o_tau);
+  q.rinv = ctx->at<double>(L.o_rinv);
+  q.flags = ctx->at<unsigned>(L.o_flags);
+  q.epoch = ctx->at<unsigned>(L.o_epoch);
+  q.status = ctx->at<int>(L.o_status);
+  q.spin_limit = SPIN_LIMIT;
+  CU(ctx->kt->qr(q, ctx->stream));
+  ph_end(ctx, MDN_PHASE_QR, 2);
+  FsParams f{};
+  f.n = ctx->n;
+  f.D = ctx->D;
+  f.rhs_sign = sgn;
+  f.A = A;
+  f.NA = D * n * n;
+  f.W = q.W;
+  f.Nnn = n * n;
+  f.rhs = rhs;
+  f.r = ctx->at<double>(L.o_r);
+  f.dx = dx;
+  f.Nx = n * D;
+  f.resabs = ctx->at<double>(L.o_resabs);
+  ph_begin(ctx, MDN_PHASE_FORWARD);
+  for (int k = 0; k < ctx->D; ++k) {
+    CU(ctx->kt->fs(f, k, ctx->stream));
+    CU(ctx->kt->fx(f, k, ctx->stream));
+  }
+  CU(ctx->kt->fs(f, ctx->D, ctx->stream));  // residual of the last stage
+  ph_end(ctx, MDN_PHASE_FORWARD, 2 * ctx->D + 1);
+  return MDN_OK;
+}
+
+static mdn_status read_status(mdn_ctx* ctx) {
+  int st = 0;
+  CU(cudaMemcpyAsync(&st, ctx->at<int>(ctx->L.o_status), 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (st & MDN_DEV_TIMEOUT) return fail(ctx, MDN_ETIMEOUT, "a bounded device wait timed out");
+  if (st & MDN_DEV_SINGULAR) return fail(ctx, MDN_ESINGULAR, "zero pivot in the Householder QR of A0");
+  if (st & MDN_DEV_NONFINITE) return fail(ctx, MDN_ENONFINITE, "non-finite value in the series");
+  return MDN_OK;
+}
+
+mdn_status mdn_newton(mdn_ctx* ctx, int max_steps, double tol, int* steps_done, double* res_hist) {
+  if (!ctx) return MDN_EINVAL;
+  if (steps_done) *steps_done = 0;
+  if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
+  if (!ctx->has_series) return fail(ctx, MDN_ESTATE, "no series set");
+  if (max_steps < 1 || max_steps > MDN_MAX_STEPS) return fail(ctx, MDN_EINVAL, "max_steps out of range");
+  const Layout& L = ctx->L;
+  const long long D = ctx->D, n = ctx->n;
+  double* x = ctx->at<double>(L.o_x);
+  double* f = ctx->at<double>(L.o_f);
+  double* dx = ctx->at<double>(L.o_dx);
+  double* A = ctx->at<double>(L.o_A);
+  double* hist = ctx->at<double>(L.o_hist);
+  CU(cudaMemsetAsync(ctx->at<int>(L.o_status), 0, 4, ctx->stream));
+  int done = 0;
+  bool converged = false;
+  for (int s = 0; s < max_steps; ++s) {
+    mdn_status r = run_evaluate(ctx, x, f, A);
+    if (r != MDN_OK) return r;
+    r = run_solve(ctx, A, f, -1, dx);
+    if (r != MDN_OK) return r;
+    UpdParams u{};
+    u.n = ctx->n;
+    u.D = ctx->D;
+    u.x = x;
+    u.dx = dx;
+    u.f = f;
+    u.Nx = n * D;
+    u.dxabs = ctx->at<double>(L.o_dxabs);
+    u.fabs = ctx->at<double>(L.o_fabs);
+    u.status = ctx->at<int>(L.o_status);
+    ph_begin(ctx, MDN_PHASE_UPDATE);
+    CU(ctx->kt->update(u, ctx->stream));
+    NormParams np{};
+    np.count = n * D;
+    np.fabs = u.fabs;
+    np.resabs = ctx->at<double>(L.o_resabs);
+    np.dxabs = u.dxabs;
+    np.hist = hist + 3 * s;
+    norms_kernel<<<1, 1024, 0, ctx->stream>>>(np);
+    CU(cudaGetLastError());
+    ph_end(ctx, MDN_PHASE_UPDATE, 2);
+    done = s + 1;
+    if (tol > 0.0) {
+      double h[3];
+      CU(cudaMemcpyAsync(h, hist + 3 * s, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+      if (h[2] <= tol) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  if (res_hist) CU(cudaMemcpyAsync(res_hist, hist, sizeof(double) * 3 * done, cudaMemcpyDeviceToHost, ctx->stream));
+  mdn_status st = read_status(ctx);
+  if (steps_done) *steps_done = done;
+  if (st != MDN_OK) return st;
+  if (tol > 0.0 && !converged) return fail(ctx, MDN_ENOTCONVERGED, "||dx||_1 above tol after %d steps", done);
+  return MDN_OK;
+}
+
+mdn_status mdn_get_residual(mdn_ctx* ctx, double* f_out) {
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->loaded || !ctx->has_series) return fail(ctx, MDN_ESTATE, "no system or series");
+  if (!f_out) return fail(ctx, MDN_EINVAL, "null output");
+  return run_evaluate(ctx, ctx->at<double>(ctx->L.o_x), f_out, nullptr);
+}
+
+mdn_status mdn_evaluate(mdn_ctx* ctx, const double* x, double* f_out, double* A_out) {
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
+  if (!x || !f_out) return fail(ctx, MDN_EINVAL, "null pointer argument");
+  return run_evaluate(ctx, x, f_out, A_out);
+}
+
+mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx) {
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
+  if (!A || !b || !dx) return fail(ctx, MDN_EINVAL, "null pointer argument");
+  CU(cudaMemsetAsync(ctx->at<int>(ctx->L.o_status), 0, 4, ctx->stream));
+  mdn_status r = run_solve(ctx, A, b, +1, dx);
+  if (r != MDN_OK) return r;
+  return read_status(ctx);
+}
+
+mdn_status mdn_status_word(mdn_ctx* ctx) {
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
+  return read_status(ctx);
+}
+
+mdn_status mdn_profile(mdn_ctx* ctx, int enable, double* ms_out, int64_t* launches_out) {
+  if (!ctx) return MDN_EINVAL;
+  if (enable) {
+    ctx->prof = true;
+    ctx->prof_rec.clear();
+    ctx->ev_used = 0;
+    ctx->open_phase = -1;
+    for (int i = 0; i < MDN_NUM_PHASES; ++i) ctx->launches[i] = 0;
+    return MDN_OK;
+  }
+  ctx->prof = false;
+  double ms[MDN_NUM_PHASES] = {0, 0, 0, 0, 0};
+  if (!ctx->prof_rec.empty()) {
+    CU(cudaEventSynchronize(ctx->prof_rec.back().second.second));
+    for (auto& r : ctx->prof_rec) {
+      float t = 0.f;
+      CU(cudaEventElapsedTime(&t, r.second.first, r.second.second));
+      ms[r.first] += t;
+    }
+  }
+  for (int i = 0; i < MDN_NUM_PHASES; ++i) {
+    if (ms_out) ms_out[i] = ms[i];
+    if (launches_out) launches_out[i] = ctx->launches[i];
+  }
+  ctx->prof_rec.clear();
+  ctx->ev_used = 0;
+  return MDN_OK;
+}
+
+const char* mdn_last_error(const mdn_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void mdn_destroy(mdn_ctx* ctx) {
+  if (!ctx) return;
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+}  // extern "C"

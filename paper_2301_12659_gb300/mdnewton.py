@@ -1,0 +1,247 @@
+"""Python binding of libmdnewton (include/mdnewton.h): argument marshalling only.
+
+Every function keeps the name and argument order of its C entry point;
+device buffers are passed as torch CUDA tensors (float64, contiguous, the
+[K][C][...] structure-of-arrays layout of the header) and host structure
+arrays as numpy int32 arrays.  All arithmetic runs in the CUDA kernels; there
+is no CPU path: loading fails loudly when the library has not been built.
+
+``Newton`` bundles the buffers a user needs (workspace, system, series) on
+top of these calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "_build", f"libmdnewton-{platform.machine()}.so")
+
+STATUS = {0: "MDN_OK", 1: "MDN_EINVAL", 2: "MDN_ECUDA", 3: "MDN_ESINGULAR", 4: "MDN_ENONFINITE",
+          5: "MDN_ENOTCONVERGED", 6: "MDN_ETIMEOUT", 7: "MDN_ESTATE", 8: "MDN_EWORKSPACE"}
+MDN_OK, MDN_EINVAL, MDN_ECUDA, MDN_ESINGULAR, MDN_ENONFINITE, MDN_ENOTCONVERGED, MDN_ETIMEOUT, \
+    MDN_ESTATE, MDN_EWORKSPACE = range(9)
+MDN_MAX_STEPS = 64
+MDN_MAX_DEGREE = 63
+
+EXPORTS = ("mdn_create", "mdn_workspace_bytes", "mdn_load_system", "mdn_set_series", "mdn_newton",
+           "mdn_get_series", "mdn_get_residual", "mdn_evaluate", "mdn_solve", "mdn_profile",
+           "mdn_status_word", "mdn_last_error", "mdn_destroy")
+MDN_NUM_PHASES = 5
+PHASES = ("evaluate", "assemble", "qr", "forward", "update")
+
+_lib = None
+
+
+class MdnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = None) -> ctypes.CDLL:
+    """Load the shared library (built by paper_2301_12659_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIBPATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmdnewton is not built ({path} missing): run paper_2301_12659_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.mdn_create.argtypes = [ctypes.POINTER(P), I, I, I, I]
+    L.mdn_workspace_bytes.argtypes = [P, I, P]
+    L.mdn_workspace_bytes.restype = ctypes.c_size_t
+    L.mdn_load_system.argtypes = [P, I, P, P, P, P, P, P, ctypes.c_size_t, P]
+    L.mdn_set_series.argtypes = [P, P]
+    L.mdn_newton.argtypes = [P, I, D, ctypes.POINTER(I), P]
+    L.mdn_get_series.argtypes = [P, P]
+    L.mdn_get_residual.argtypes = [P, P]
+    L.mdn_evaluate.argtypes = [P, P, P, P]
+    L.mdn_solve.argtypes = [P, P, P, P]
+    L.mdn_profile.argtypes = [P, I, P, P]
+    L.mdn_status_word.argtypes = [P]
+    L.mdn_last_error.argtypes = [P]
+    L.mdn_last_error.restype = ctypes.c_char_p
+    L.mdn_destroy.argtypes = [P]
+    for name in EXPORTS:
+        if name not in ("mdn_workspace_bytes", "mdn_last_error", "mdn_destroy"):
+            getattr(L, name).restype = I
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    """Device pointer of a tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype.is_floating_point and str(t.dtype) != "torch.float64":
+        raise TypeError("expected a float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(ctx, status: int):
+    if status != MDN_OK:
+        raise MdnError(status, mdn_last_error(ctx))
+
+
+# ---- the C entry points -----------------------------------------------------
+
+def mdn_create(limbs: int, is_complex: int, n: int, degree: int):
+    h = ctypes.c_void_p()
+    st = load().mdn_create(ctypes.byref(h), int(limbs), int(is_complex), int(n), int(degree))
+    if st != MDN_OK:
+        raise MdnError(st, f"mdn_create(limbs={limbs}, is_complex={is_complex}, n={n}, degree={degree})")
+    return h
+
+
+def mdn_workspace_bytes(ctx, n_monomials: int, var_ptr) -> int:
+    arr, p = _host_i32(var_ptr)
+    return int(load().mdn_workspace_bytes(ctx, int(n_monomials), p))
+
+
+def mdn_load_system(ctx, n_monomials, eq_of_monomial, var_ptr, var_idx, coeff, const_term, workspace,
+                    ws_bytes, cuda_stream) -> int:
+    eq, peq = _host_i32(eq_of_monomial)
+    vp, pvp = _host_i32(var_ptr)
+    vi, pvi = _host_i32(var_idx)
+    return load().mdn_load_system(ctx, int(n_monomials), peq, pvp, pvi, _ptr(coeff), _ptr(const_term),
+                                  ctypes.c_void_p(workspace.data_ptr()), int(ws_bytes),
+                                  ctypes.c_void_p(int(cuda_stream)))
+
+
+def mdn_set_series(ctx, x) -> int:
+    return load().mdn_set_series(ctx, _ptr(x))
+
+
+def mdn_newton(ctx, max_steps: int, tol: float = 0.0):
+    """Returns (status, steps_done, hist[steps_done, 3])."""
+    done = ctypes.c_int(0)
+    hist = np.zeros((max(int(max_steps), 1), 3))
+    st = load().mdn_newton(ctx, int(max_steps), float(tol), ctypes.byref(done), hist.ctypes.data_as(ctypes.c_void_p))
+    return st, done.value, hist[:done.value]
+
+
+def mdn_get_series(ctx, x_out) -> int:
+    return load().mdn_get_series(ctx, _ptr(x_out))
+
+
+def mdn_get_residual(ctx, f_out) -> int:
+    return load().mdn_get_residual(ctx, _ptr(f_out))
+
+
+def mdn_evaluate(ctx, x, f_out, A_out=None) -> int:
+    return load().mdn_evaluate(ctx, _ptr(x), _ptr(f_out), _ptr(A_out))
+
+
+def mdn_solve(ctx, A, b, dx) -> int:
+    return load().mdn_solve(ctx, _ptr(A), _ptr(b), _ptr(dx))
+
+
+def mdn_profile(ctx, enable: int):
+    """enable=1 starts the phase timers; enable=0 stops them and returns
+    (status, ms per phase, kernel launches per phase)."""
+    ms = np.zeros(MDN_NUM_PHASES)
+    launches = np.zeros(MDN_NUM_PHASES, dtype=np.int64)
+    st = load().mdn_profile(ctx, int(enable), ms.ctypes.data_as(ctypes.c_void_p),
+                            launches.ctypes.data_as(ctypes.c_void_p))
+    return st, ms, launches
+
+
+def mdn_status_word(ctx) -> int:
+    return load().mdn_status_word(ctx)
+
+
+def mdn_last_error(ctx) -> str:
+    return load().mdn_last_error(ctx).decode()
+
+
+def mdn_destroy(ctx) -> None:
+    load().mdn_destroy(ctx)
+
+
+# ---- convenience -------------------------------------------------------------
+
+class Newton:
+    """A loaded system on the current CUDA device: owns the device buffers
+    (workspace, coefficient and constant series) as torch tensors."""
+
+    def __init__(self, system, stream=None):
+        import torch
+
+        self.torch = torch
+        s = system
+        self.K, self.C, self.n, self.d = s.K, s.C, s.n, s.d
+        self.shape_series = (s.K, s.C, s.n, s.d + 1)
+        self.shape_A = (s.K, s.C, s.d + 1, s.n, s.n)
+        self.ctx = mdn_create(s.K, s.C - 1, s.n, s.d)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream or torch.cuda.current_stream()
+        self.ws_bytes = mdn_workspace_bytes(self.ctx, s.M, s.vptr)
+        if self.ws_bytes == 0:
+            raise MdnError(MDN_EINVAL, "workspace size")
+        self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=dev)
+        off = (-self.workspace.data_ptr()) % 256
+        self.workspace = self.workspace[off:off + self.ws_bytes]
+        self.coeff = torch.as_tensor(np.ascontiguousarray(s.coeff), device=dev)
+        cst = s.cst if s.cst is not None else np.zeros(self.shape_series)
+        self.cst = torch.as_tensor(np.ascontiguousarray(cst), device=dev)
+        _check(self.ctx, mdn_load_system(self.ctx, s.M, s.eq, s.vptr, s.vidx, self.coeff, self.cst,
+                                         self.workspace, self.ws_bytes, self.stream.cuda_stream))
+
+    def set_constant(self, cst):
+        """Replace the constant term series (device copy, same shape)."""
+        self.cst.copy_(cst if isinstance(cst, self.torch.Tensor) else self.torch.as_tensor(cst))
+
+    def set_series(self, x):
+        x = x if isinstance(x, self.torch.Tensor) else self.torch.as_tensor(np.ascontiguousarray(x), device=self.cst.device)
+        self._x_in = x.contiguous()
+        _check(self.ctx, mdn_set_series(self.ctx, self._x_in))
+
+    def newton(self, steps: int, tol: float = 0.0):
+        st, done, hist = mdn_newton(self.ctx, steps, tol)
+        if st not in (MDN_OK,):
+            raise MdnError(st, mdn_last_error(self.ctx))
+        return hist
+
+    def series(self):
+        x = self.torch.empty(self.shape_series, dtype=self.torch.float64, device=self.cst.device)
+        _check(self.ctx, mdn_get_series(self.ctx, x))
+        return x
+
+    def evaluate(self, x, want_A: bool = True):
+        dev = self.cst.device
+        x = x if isinstance(x, self.torch.Tensor) else self.torch.as_tensor(np.ascontiguousarray(x), device=dev)
+        f = self.torch.empty(self.shape_series, dtype=self.torch.float64, device=dev)
+        A = self.torch.empty(self.shape_A, dtype=self.torch.float64, device=dev) if want_A else None
+        _check(self.ctx, mdn_evaluate(self.ctx, x.contiguous(), f, A))
+        return (f, A) if want_A else f
+
+    def solve(self, A, b):
+        dev = self.cst.device
+        A = A if isinstance(A, self.torch.Tensor) else self.torch.as_tensor(np.ascontiguousarray(A), device=dev)
+        b = b if isinstance(b, self.torch.Tensor) else self.torch.as_tensor(np.ascontiguousarray(b), device=dev)
+        dx = self.torch.empty(self.shape_series, dtype=self.torch.float64, device=dev)
+        _check(self.ctx, mdn_solve(self.ctx, A.contiguous(), b.contiguous(), dx))
+        return dx
+
+    def close(self):
+        if self.ctx is not None:
+            mdn_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

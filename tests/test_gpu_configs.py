@@ -1,0 +1,89 @@
+"""The three plain Newton workloads at full size through the C-ABI.
+
+* double double, n=8, d=15: GPU Newton (6 steps) against the oracle's Newton,
+  entry by entry, and against the planted solution, tolerance 1e-28;
+* quad double, n=64, d=31: evaluation and differentiation at the start
+  series against the oracle (all of f and A), 7 GPU Newton steps against the
+  oracle's 7 steps and against the planted solution, tolerance 1e-58;
+* complex octo double, n=128, d=63: rows of f at a random series against the
+  oracle (a sample: the oracle needs minutes per equation set), and Newton
+  from the start series recovering the planted solution of the system whose
+  constant term the library evaluates itself (a convergence property, not
+  parity), tolerance 1e-118, with the error of x_0 squaring per step.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2301_12659_gb300 import workloads as wl
+from tests import metrics as mt
+from tests.gpu_util import need_gpu, planted, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def md():
+    return need_gpu()
+
+
+def test_dd_real_n8_d15(md):
+    cfg = wl.CONFIGS["dd-real-n8-d15"]
+    s, xstar, x0 = planted(cfg)
+    x_ref, h_ref = oracle.newton(s, x0, cfg.steps)
+    nw = md.Newton(s)
+    nw.set_series(x0)
+    hist = nw.newton(cfg.steps)
+    x = to_np(nw.series())
+    assert np.max(mt.series_rel_error(x, x_ref)) <= cfg.tol
+    assert np.max(mt.series_rel_error(x, xstar)) <= cfg.tol
+    assert np.allclose(hist[:3, 0], h_ref[:3, 0], rtol=1e-12)
+
+
+def test_qd_real_n64_d31(md):
+    cfg = wl.CONFIGS["qd-real-n64-d31"]
+    s, xstar, x0 = planted(cfg)
+    nw = md.Newton(s)
+    f_ref, A_ref = oracle.evaluate(s, x0)
+    f, A = nw.evaluate(x0)
+    assert mt.matrix_rel_error(to_np(f), f_ref) <= cfg.tol
+    assert mt.matrix_rel_error(to_np(A), A_ref) <= cfg.tol
+    nw.set_series(x0)
+    hist = nw.newton(cfg.steps)
+    x = to_np(nw.series())
+    assert np.max(mt.series_rel_error(x, xstar)) <= cfg.tol
+    x_ref, h_ref = oracle.newton(s, x0, cfg.steps)
+    assert np.max(mt.series_rel_error(x, x_ref)) <= cfg.tol
+    assert np.allclose(hist[:4, 0], h_ref[:4, 0], rtol=1e-12)
+
+
+def test_od_complex_n128_d63(md):
+    import torch
+    cfg = wl.CONFIGS["od-complex-n128-d63"]
+    s, xstar, x0 = wl.planted_system(cfg)
+    s.cst = np.zeros((s.K, s.C, s.n, s.D))
+    nw = md.Newton(s)
+    # sampled parity: rows 0 and 77 of f at a random series
+    x = wl.random_md((s.n, s.D), s.K, s.C, 99, unit_circle=True)
+    f = to_np(nw.evaluate(x, want_A=False))
+    rows = [0, 77]
+    keep = np.isin(s.eq, rows)
+    sub = wl.System(s.K, s.C, s.n, s.d, s.eq[keep], None, None, s.coeff[:, :, keep], s.cst)
+    sizes = np.diff(s.vptr)[keep]
+    sub.vptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    sub.vidx = np.concatenate([s.vidx[s.vptr[m]:s.vptr[m + 1]] for m in np.nonzero(keep)[0]]).astype(np.int32)
+    f_ref = oracle.evaluate(sub, x, want_A=False)
+    assert mt.matrix_rel_error(f[:, :, rows], f_ref[:, :, rows]) <= cfg.tol
+    # Newton recovers the plant of the library's own evaluation
+    cst = -nw.evaluate(xstar, want_A=False)
+    nw.set_constant(cst)
+    nw.set_series(x0)
+    errs = []
+    for _ in range(cfg.steps):
+        nw.newton(1)
+        errs.append(float(np.max(mt.series_rel_error(to_np(nw.series()), xstar)[:, 0])))
+    x = to_np(nw.series())
+    assert np.max(mt.series_rel_error(x, xstar)) <= cfg.tol
+    for a, b in zip(errs, errs[1:]):
+        if a > 1e3 * cfg.tol:
+            assert b <= max(1e4 * a * a, cfg.tol), errs

@@ -1,0 +1,176 @@
+"""GPU path (through the C-ABI) against the CPU oracle, element by element,
+on seeded inputs: evaluation and differentiation, the block Toeplitz solve
+and whole Newton runs, over limbs, real/complex data, ragged degrees and
+sizes that span several warps and waves, and the degenerate cases.
+
+Tolerances: the stated per-coefficient bars 1e-28 (dd), 1e-58 (qd) and
+1e-118 (od), normalised by max(|y_k|, series or matrix scale)."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2301_12659_gb300 import workloads as wl
+from tests import metrics as mt
+from tests import systems as ts
+from tests.gpu_util import TOL, need_gpu, planted, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def md():
+    return need_gpu()
+
+
+def _newton(md, s):
+    return md.Newton(s)
+
+
+EVAL_CASES = [
+    # K, C, n, d, monomials per equation, kmin, kmax
+    (1, 1, 5, 7, 3, 1, 3),
+    (2, 1, 8, 15, 4, 3, 3),
+    (2, 1, 3, 0, 2, 1, 3),       # d = 0: one coefficient (plain md products)
+    (2, 2, 6, 10, 3, 1, 4),      # odd D = 11: ragged lane groups
+    (4, 1, 17, 31, 5, 2, 8),     # n not a multiple of the warp
+    (4, 2, 5, 20, 3, 1, 5),
+    (8, 1, 4, 63, 2, 1, 5),      # D = 64: one product per warp
+    (8, 2, 3, 12, 2, 2, 4),
+]
+
+
+@pytest.mark.parametrize("K,C,n,d,mpe,kmin,kmax", EVAL_CASES)
+def test_evaluate_matches_oracle(md, K, C, n, d, mpe, kmin, kmax):
+    cfg = wl.small_config(K, C, n=n, d=d, mono_per_eq=mpe, kmin=kmin, kmax=kmax, index=700 + K + 10 * C + n)
+    s, xstar, x0 = planted(cfg)
+    x = wl.random_md((n, d + 1), K, C, 31 + n, unit_circle=(C == 2))
+    f_ref, A_ref = oracle.evaluate(s, x)
+    nw = _newton(md, s)
+    f, A = nw.evaluate(x)
+    assert mt.matrix_rel_error(to_np(f), f_ref) <= TOL[K]
+    assert mt.matrix_rel_error(to_np(A), A_ref) <= TOL[K]
+
+
+def test_evaluate_powers_and_single_variable_monomials(md):
+    """Repeated variables are powers (their partials add up); one-variable
+    monomials have the coefficient series as partial."""
+    K, C, n, d = 4, 1, 3, 9
+    D = d + 1
+    eq = np.array([0, 0, 1, 2, 2], np.int32)
+    vptr = np.array([0, 3, 4, 6, 7, 9], np.int32)
+    vidx = np.array([0, 0, 1, 2, 1, 1, 2, 0, 2], np.int32)   # x0^2 x1, x2, x1^2, x2, x0 x2
+    coeff = wl.random_md((5, D), K, C, 5)
+    s = wl.System(K, C, n, d, eq, vptr, vidx, coeff, wl.random_md((n, D), K, C, 6))
+    x = wl.random_md((n, D), K, C, 7)
+    f_ref, A_ref = oracle.evaluate(s, x)
+    f, A = _newton(md, s).evaluate(x)
+    assert mt.matrix_rel_error(to_np(f), f_ref) <= TOL[K]
+    assert mt.matrix_rel_error(to_np(A), A_ref) <= TOL[K]
+
+
+def test_speelpenning_on_gpu(md):
+    """prod_{i<8} x_i at x_i = 1 + t: binomial coefficients, exactly."""
+    from math import comb
+    K, k, D = 4, 8, 12
+    s = wl.System(K, 1, k, D - 1, np.zeros(1, np.int32), np.array([0, k], np.int32), np.arange(k, dtype=np.int32),
+                  np.zeros((K, 1, 1, D)), np.zeros((K, 1, k, D)))
+    s.coeff[0, 0, 0, 0] = 1.0
+    x = np.zeros((K, 1, k, D))
+    x[0, 0, :, 0] = 1.0
+    x[0, 0, :, 1] = 1.0
+    f, A = _newton(md, s).evaluate(x)
+    f, A = to_np(f), to_np(A)
+    for j in range(D):
+        assert f[0, 0, 0, j] == comb(k, j) and np.all(f[1:, 0, 0, j] == 0)
+        assert np.all(A[0, 0, j, 0, :] == comb(k - 1, j)) and np.all(A[1:, 0, j, 0, :] == 0)
+
+
+SOLVE_CASES = [(2, 1, 7, 15), (4, 1, 33, 31), (4, 2, 9, 7), (8, 1, 5, 20), (8, 2, 4, 5), (2, 1, 1, 0)]
+
+
+@pytest.mark.parametrize("K,C,n,d", SOLVE_CASES)
+def test_solve_matches_oracle(md, K, C, n, d):
+    D = d + 1
+    A = wl.random_md((D, n, n), K, C, 40 + n, unit_circle=False)
+    for i in range(n):
+        A[0, 0, 0, i, i] += n
+    b = wl.random_md((n, D), K, C, 41 + n)
+    dx_ref = oracle.solve(A, b)
+    # any system gives a context of the right shape
+    cfg = wl.small_config(K, C, n=n, d=d, mono_per_eq=1, kmin=1, kmax=1, index=800)
+    s, _, _ = planted(cfg, with_cst=False)
+    dx = _newton(md, s).solve(A, b)
+    assert np.max(mt.series_rel_error(to_np(dx), dx_ref)) <= TOL[K]
+
+
+def test_singular_A0_is_reported(md):
+    K, C, n, d = 2, 1, 4, 3
+    A = wl.random_md((d + 1, n, n), K, C, 3)
+    A[:, :, 0, :, 2] = 0.0        # zero column of A0
+    b = wl.random_md((n, d + 1), K, C, 4)
+    cfg = wl.small_config(K, C, n=n, d=d, mono_per_eq=1, kmin=1, kmax=1, index=801)
+    s, _, _ = planted(cfg, with_cst=False)
+    nw = _newton(md, s)
+    with pytest.raises(md.MdnError) as e:
+        nw.solve(A, b)
+    assert e.value.status == md.MDN_ESINGULAR
+
+
+def test_nonfinite_series_is_reported(md):
+    cfg = wl.small_config(2, 1, n=4, d=5, index=802)
+    s, xstar, x0 = planted(cfg)
+    nw = _newton(md, s)
+    x0 = x0.copy()
+    x0[0, 0, 1, 0] = np.nan
+    nw.set_series(x0)
+    with pytest.raises(md.MdnError) as e:
+        nw.newton(1)
+    assert e.value.status in (md.MDN_ENONFINITE, md.MDN_ESINGULAR)
+
+
+NEWTON_CASES = [
+    wl.small_config(2, 1, n=4, d=7, mono_per_eq=3, kmin=1, kmax=3, steps=6, index=500),
+    wl.small_config(4, 1, n=5, d=9, mono_per_eq=3, kmin=2, kmax=4, steps=7, index=501),
+    wl.small_config(8, 2, n=3, d=5, mono_per_eq=2, kmin=1, kmax=3, steps=8, index=502),
+    wl.small_config(4, 2, n=6, d=13, mono_per_eq=3, kmin=1, kmax=4, steps=7, index=503),
+    wl.small_config(2, 1, n=40, d=15, mono_per_eq=4, kmin=2, kmax=6, steps=6, index=504),
+]
+
+
+@pytest.mark.parametrize("cfg", NEWTON_CASES, ids=lambda c: c.name)
+def test_newton_matches_oracle_and_plant(md, cfg):
+    s, xstar, x0 = planted(cfg)
+    x_ref, h_ref = oracle.newton(s, x0, cfg.steps)
+    nw = _newton(md, s)
+    nw.set_series(x0)
+    hist = nw.newton(cfg.steps)
+    x = to_np(nw.series())
+    assert np.max(mt.series_rel_error(x, x_ref)) <= cfg.tol
+    assert np.max(mt.series_rel_error(x, xstar)) <= cfg.tol
+    # ||f|| before each update agrees where it is above the rounding level
+    big = h_ref[:, 0] > 1e-6
+    assert np.allclose(hist[big, 0], h_ref[big, 0], rtol=1e-10)
+    assert hist[-1, 0] < 1e3 * cfg.tol and hist[-1, 1] < 1e3 * cfg.tol
+
+
+@pytest.mark.parametrize("K", [2, 4])
+def test_newton_sqrt_one_plus_t(md, K):
+    s, sol, x0 = ts.sqrt_system(K, 15 if K == 2 else 31)
+    nw = _newton(md, s)
+    nw.set_series(x0)
+    nw.newton(6 if K == 2 else 7)
+    x = to_np(nw.series())
+    assert np.max(mt.series_rel_error(x, ts.solution_md(sol, K, 1))) <= TOL[K]
+
+
+def test_newton_two_column_complex(md):
+    from fractions import Fraction as Fr
+    alphas = [(Fr(3, 5), Fr(4, 5)), (Fr(-4, 5), Fr(3, 5)), (Fr(-1), Fr(0))]
+    c1 = [(Fr(3, 4), Fr(1, 4)), (Fr(-5, 4), Fr(0)), (Fr(1, 2), Fr(-1, 2))]
+    c2 = [(Fr(3, 8), Fr(0)), (Fr(1), Fr(1, 8)), (Fr(-5, 8), Fr(1, 4))]
+    s, sol, x0 = ts.two_column_system(4, 2, alphas, c1, c2, 31)
+    nw = _newton(md, s)
+    nw.set_series(x0)
+    nw.newton(8)
+    x = to_np(nw.series())
+    assert np.max(mt.series_rel_error(x, ts.solution_md(sol, 4, 2))) <= TOL[4]

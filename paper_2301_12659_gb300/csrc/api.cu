@@ -166,7 +166,7 @@ struct Layout {
   size_t total = 0;
   size_t o_order, o_mono_k, o_mono_vp, o_mono_sbase, o_vidx, o_sched, o_sched_off, o_sched_nw, o_eq_ptr,
       o_eq_mon, o_pair_ptr, o_pair_slot, o_occ, o_counter, o_status, o_flags, o_epoch, o_done;
-  size_t o_x, o_f, o_dx, o_r, o_out, o_out0, o_scratch, o_A, o_Rm, o_Vm, o_Y, o_W, o_tau, o_rinv, o_fabs, o_dxabs,
+  size_t o_x, o_f, o_dx, o_r, o_out, o_out0, o_scratch, o_A, o_Rm, o_Vm, o_Y, o_Z, o_W, o_tau, o_rinv, o_salpha, o_v0, o_fabs, o_dxabs,
       o_resabs, o_hist;
 };
 
@@ -353,7 +353,7 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_occ = take(4 * (size_t)ctx->nnz);
   L.o_counter = take(4);
   L.o_status = take(4);
-  L.o_flags = take(4 * 2 * n);
+  L.o_flags = take(4 * 3 * n);
   L.o_epoch = take(4);
   L.o_done = take(4 * 2 * D);
   const size_t ser = 8 * KC * n * D;
@@ -368,9 +368,12 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_Rm = take(8 * KC * n * n);
   L.o_Vm = take(8 * KC * n * n);
   L.o_Y = take(8 * KC * n * n);
+  L.o_Z = take(8 * KC * n * n);
   L.o_W = take(8 * KC * n * n);
   L.o_tau = take(8 * (size_t)ctx->K * n);
   L.o_rinv = take(8 * KC * n);
+  L.o_salpha = take(8 * KC * n);
+  L.o_v0 = take(8 * KC * n);
   L.o_fabs = take(8 * n * D);
   L.o_dxabs = take(8 * n * D);
   L.o_resabs = take(8 * n * D);
@@ -385,7 +388,9 @@ mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degre
   *out = nullptr;
   const int C = is_complex ? 2 : 1;
   const KernelTable* kt = kernels_for(limbs, C);
-  if (!kt || n < 1 || n > 4096 || degree < 0 || degree > MDN_MAX_DEGREE) return MDN_EINVAL;
+  if (!kt || n < 1 || n > MDN_MAX_N || degree < 0 || degree > MDN_MAX_DEGREE) return MDN_EINVAL;
+  // the QR keeps one column per warp, four warps per block, in shared memory
+  if ((size_t)4 * n * 2 * limbs * sizeof(double) > (size_t)QR_SMEM_RESERVE) return MDN_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MDN_ECUDA;
   int sms = 0;
@@ -466,7 +471,7 @@ mdn_status mdn_load_system(mdn_ctx* ctx, int M, const int32_t* eq, const int32_t
   CU(put(L.o_occ, ctx->occ.data(), 4 * ctx->occ.size()));
   CU(cudaMemsetAsync(ctx->ws + L.o_counter, 0, 4, st));
   CU(cudaMemsetAsync(ctx->ws + L.o_status, 0, 4, st));
-  CU(cudaMemsetAsync(ctx->ws + L.o_flags, 0, 4 * 2 * (size_t)ctx->n, st));
+  CU(cudaMemsetAsync(ctx->ws + L.o_flags, 0, 4 * 3 * (size_t)ctx->n, st));
   CU(cudaMemsetAsync(ctx->ws + L.o_epoch, 0, 4, st));
   CU(cudaMemsetAsync(ctx->ws + L.o_dx, 0, 8 * (size_t)ctx->K * ctx->C * ctx->n * ctx->D, st));
   CU(cudaStreamSynchronize(st));  // host tables may be reused after return
@@ -598,9 +603,12 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A, cudaStream_t st) {
   q.Rm = ctx->at<double>(L.o_Rm);
   q.Vm = ctx->at<double>(L.o_Vm);
   q.Y = ctx->at<double>(L.o_Y);
+  q.Z = ctx->at<double>(L.o_Z);
   q.W = ctx->at<double>(L.o_W);
   q.tau = ctx->at<double>(L.o_tau);
   q.rinv = ctx->at<double>(L.o_rinv);
+  q.salpha = ctx->at<double>(L.o_salpha);
+  q.v0 = ctx->at<double>(L.o_v0);
   q.flags = ctx->at<unsigned>(L.o_flags);
   q.epoch = ctx->at<unsigned>(L.o_epoch);
   q.status = ctx->at<int>(L.o_status);
@@ -609,7 +617,7 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A, cudaStream_t st) {
   return MDN_OK;
 }
 
-static int qr_blocks(const mdn_ctx* ctx) { return 2 * ((ctx->n + (QR_THREADS / 32) - 1) / (QR_THREADS / 32)); }
+static int qr_blocks(const mdn_ctx* ctx) { return 3 * ((ctx->n + (QR_THREADS / 32) - 1) / (QR_THREADS / 32)); }
 
 // Forward substitution for dx with right hand side sgn * rhs (needs W).
 static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* rhs, int sgn, double* dx) {
@@ -647,7 +655,9 @@ static mdn_status run_step(mdn_ctx* ctx, double* x, double* f, double* A, double
   const Layout& L = ctx->L;
   const long long D = ctx->D, n = ctx->n;
   const int qb = qr_blocks(ctx);
-  const bool overlap = ctx->side && qb <= ctx->num_sms / 2;
+  // the QR of A0 runs beside the evaluation when it needs at most a third of
+  // the SMs (the evaluation keeps the rest); otherwise one after the other
+  const bool overlap = ctx->side && qb <= ctx->num_sms / 3;
   mdn_status r;
   if (overlap) {
     CU(cudaEventRecord(ctx->ev_fork, ctx->stream));
@@ -655,7 +665,7 @@ static mdn_status run_step(mdn_ctx* ctx, double* x, double* f, double* A, double
     ph_begin(ctx, MDN_PHASE_QR, ctx->side);
     if ((r = run_a0(ctx, x, A, ctx->side)) != MDN_OK) return r;
     if ((r = run_qr(ctx, A, ctx->side)) != MDN_OK) return r;
-    ph_end(ctx, MDN_PHASE_QR, 4, ctx->side);
+    ph_end(ctx, MDN_PHASE_QR, 5, ctx->side);
     CU(cudaEventRecord(ctx->ev_join, ctx->side));
     if ((r = run_evaluate(ctx, x, f, A, ctx->num_sms - qb)) != MDN_OK) return r;
     CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
@@ -664,7 +674,7 @@ static mdn_status run_step(mdn_ctx* ctx, double* x, double* f, double* A, double
     ph_begin(ctx, MDN_PHASE_QR);
     if ((r = run_a0(ctx, x, A, ctx->stream)) != MDN_OK) return r;
     if ((r = run_qr(ctx, A, ctx->stream)) != MDN_OK) return r;
-    ph_end(ctx, MDN_PHASE_QR, 4);
+    ph_end(ctx, MDN_PHASE_QR, 5);
   }
   if ((r = run_forward(ctx, A, f, -1, dx)) != MDN_OK) return r;
   UpdParams u{};
@@ -759,8 +769,10 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
   if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
   if (!A || !b || !dx) return fail(ctx, MDN_EINVAL, "null pointer argument");
   CU(cudaMemsetAsync(ctx->at<int>(ctx->L.o_status), 0, 4, ctx->stream));
+  ph_begin(ctx, MDN_PHASE_QR);
   mdn_status r = run_qr(ctx, A, ctx->stream);
   if (r != MDN_OK) return r;
+  ph_end(ctx, MDN_PHASE_QR, 3);
   if ((r = run_forward(ctx, A, b, +1, dx)) != MDN_OK) return r;
   return read_status(ctx);
 }

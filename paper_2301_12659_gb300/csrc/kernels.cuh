@@ -144,7 +144,6 @@ __device__ __forceinline__ bool warp_wait(const unsigned* flag, unsigned ep, lon
           atomicOr(status, MDN_DEV_TIMEOUT);
           break;
         }
-        __nanosleep(100);
       }
     }
   }
@@ -376,70 +375,156 @@ __global__ void a0_assemble_kernel(A0Params p) {
 // ---------------------------------------------------------------------------
 // Householder QR of A0 and W = A0^{-1} = R^{-1} Q^H (Section 5.3)
 // ---------------------------------------------------------------------------
-// Cooperative launch: CTAs [0, nA) hold one warp per column of A0, CTAs
-// [nA, 2 nA) one warp per column of the identity.  The owner of column j
-// publishes reflector j (v_j, tau_j = 2 / v_j^H v_j) with a release flag;
-// the other columns apply H_j = I - tau_j v_j v_j^H as soon as it appears.
-// v_j = x + s |x| e_1 with s = x_0 / |x_0| (+1 for x_0 = 0), so that
-// H_j x = -s |x| e_1.  tau_j = 1 / (|x| (|x| + |x_0|)).
+// Cooperative launch, one block per SM, three roles of nA blocks each:
+// one warp per column of A0, one warp per column of the identity (Q^H), one
+// warp per row of R^{-1}.  Every warp keeps its column or row in shared
+// memory, limb by limb (structure of arrays, conflict free).
+//
+// Reflector j is H_j = I - tau_j v_j v_j^H with v_j = x_j + s_j |x_j| e_j,
+// x_j = column j (rows j..n-1) after H_0..H_{j-1}, s_j = x_jj / |x_jj| (+1 for
+// x_jj = 0), tau_j = 1 / (|x_j| (|x_j| + |x_jj|)); then H_j x_j = -s_j |x_j| e_j.
+// Three flags per column (values = the launch epoch):
+//   col[j]  x_j is published (rows j..n-1 of Vm column j);
+//   ref[j]  the scalars s_j|x_j|, v_jj and tau_j are published;
+//   rinv[j] 1 / R_jj is published.
+// Look-ahead: the warp of column c forms x_j^H y_c (and, for j = c-1, |y_c|^2
+// over rows c-1..n-1) as soon as col[j] appears, while the owner of column j
+// is still computing its scalars; when ref[j] appears, applying H_j costs
+//   w = x_j^H y_c + conj(s_j|x_j|) y_c[j],   y_c -= tau_j w v_j,
+// and the norm of the next column follows by downdating,
+//   |y_c'[c..]|^2 = |y_c[c-1..]|^2 - |y_c'[c-1]|^2  (H_{c-1} is unitary),
+// recomputed directly if that loses more than 8 bits.
 
+// acc += conj(x_j[i]) y[i] over rows i = j..n-1 (x_j from Vm), and, if
+// with_norm, nrm += |y[i]|^2 over the same rows.
 template <int K, int C>
-__device__ void qr_apply(const QrParams& p, int j, double* y, long long Ny, long long col) {
-  // y[:, col] -= tau_j (v_j^H y) v_j over rows j..n-1
+__device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const double* y, bool with_norm,
+                                             cmd<K, C>& dot, double (&nrm)[K]) {
   const int lane = threadIdx.x & 31;
   const int n = p.n;
-  CAcc<K, C> acc;
+  CAcc<K, C> acc, an;
   cacc_zero(acc);
+  cacc_zero(an);
   for (int i = j + lane; i < n; i += 32) {
-    cmd<K, C> v, yv;
-    ld(p.Vm, p.Nnn, (long long)i * n + j, v);
-    ld(y, Ny, (long long)i * n + col, yv);
-    cacc_fma_conj(acc, v, yv);
+    cmd<K, C> x, yi;
+    ld(p.Vm, p.Nnn, (long long)i * n + j, x);
+    ld(y, n, i, yi);
+    cacc_fma_conj(acc, x, yi);
+    if (with_norm) {
+      acc_fma(an.re, yi.re, yi.re);
+      if constexpr (C == 2) acc_fma(an.re, yi.im, yi.im);
+    }
   }
-  cmd<K, C> w, g;
-  warp_sum_acc(acc, w);
+  warp_sum_acc(acc, dot);
+  if (with_norm) {
+    cmd<K, C> t;
+    warp_sum_acc(an, t);
+    md_copy(t.re, nrm);
+  }
+}
+
+// y -= tau_j w v_j with w = dot + conj(salpha_j) y[j] (rows j..n-1).
+template <int K, int C>
+__device__ __forceinline__ void qr_apply_la(const QrParams& p, int j, double* y, const cmd<K, C>& dot) {
+  const int lane = threadIdx.x & 31;
+  const int n = p.n;
+  cmd<K, C> sa, vj0, yj, w, g, ng;
+  ld(p.salpha, p.n, j, sa);
+  ld(p.v0, p.n, j, vj0);
   double tau[K];
   ld_real(p.tau, p.n, j, tau);
+  ld(y, n, j, yj);
+  CAcc<K, C> a;
+  cacc_set(a, dot);
+  cacc_fma_conj(a, sa, yj);
+  cacc_get(a, w);
   cmd_scale(w, tau, g);
-  cmd<K, C> ng;
   md_neg(g.re, ng.re);
   md_neg(g.im, ng.im);
+  __syncwarp();
   for (int i = j + lane; i < n; i += 32) {
-    cmd<K, C> v, yv;
-    ld(p.Vm, p.Nnn, (long long)i * n + j, v);
-    ld(y, Ny, (long long)i * n + col, yv);
-    CAcc<K, C> a2;
-    cacc_set(a2, yv);
-    cacc_fma(a2, ng, v);
-    cacc_get(a2, yv);
-    st(y, Ny, (long long)i * n + col, yv);
+    cmd<K, C> v, yi;
+    if (i == j) v = vj0;
+    else ld(p.Vm, p.Nnn, (long long)i * n + j, v);
+    ld(y, n, i, yi);
+    CAcc<K, C> b;
+    cacc_set(b, yi);
+    cacc_fma(b, ng, v);
+    cacc_get(b, yi);
+    st(y, n, i, yi);
   }
   __syncwarp();
 }
 
+// Column warp c: its column under the reflectors 0..c-1, then reflector c.
 template <int K, int C>
-__device__ void qr_reflector(const QrParams& p, int j, unsigned ep) {
+__device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
   const int lane = threadIdx.x & 31;
   const int n = p.n;
-  // N = |x|^2 over rows j..n-1 of column j
-  CAcc<K, C> a2;
-  cacc_zero(a2);
-  for (int i = j + lane; i < n; i += 32) {
-    cmd<K, C> x;
-    ld(p.Rm, p.Nnn, (long long)i * n + j, x);
-    acc_fma(a2.re, x.re, x.re);
-    if constexpr (C == 2) acc_fma(a2.re, x.im, x.im);
+  unsigned* fcol = p.flags;
+  unsigned* fref = p.flags + n;
+  unsigned* frinv = p.flags + 2 * n;
+  for (int i = lane; i < n; i += 32) {
+    cmd<K, C> v;
+    ld(p.A0, p.NA, (long long)i * n + c, v);
+    st(y, n, i, v);
   }
-  cmd<K, C> nrm;
-  warp_sum_acc(a2, nrm);
-  const bool singular = !nonzero(nrm.re[0]);
-  if (singular) nrm.re[0] = 1.0;  // keep the arithmetic finite; reported below
-  // alpha = |x| = N / sqrt(N)
+  __syncwarp();
+  double pre_norm[K];
+  md_zero(pre_norm);
+  for (int j = 0; j < c; ++j) {
+    if (!warp_wait(&fcol[j], ep, p.spin_limit, p.status)) return;
+    cmd<K, C> dot;
+    qr_lookahead<K, C>(p, j, y, j == c - 1, dot, pre_norm);
+    if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
+    qr_apply_la<K, C>(p, j, y, dot);
+    if (lane == 0) {
+      cmd<K, C> v;
+      ld(y, n, j, v);
+      st(p.Rm, p.Nnn, (long long)j * n + c, v);  // R[j][c] is final
+    }
+  }
+  // publish x_c (rows c..n-1)
+  for (int i = c + lane; i < n; i += 32) {
+    cmd<K, C> v;
+    ld(y, n, i, v);
+    st(p.Vm, p.Nnn, (long long)i * n + c, v);
+  }
+  warp_publish(&fcol[c], ep);
+  // N = |x_c|^2 by downdating (direct for c = 0 or on cancellation)
+  double N[K];
+  bool direct = (c == 0);
+  if (!direct) {
+    double t[K];
+    cmd<K, C> yp;
+    ld(y, n, c - 1, yp);
+    cmd_abs2(yp, t);
+    md_sub(pre_norm, t, N);
+    // more than 8 bits lost (or a negative difference): recompute
+    const unsigned long long eN = (unsigned long long)__double_as_longlong(N[0]) >> 52;
+    const unsigned long long eP = (unsigned long long)__double_as_longlong(pre_norm[0]) >> 52;
+    direct = (__double_as_longlong(N[0]) <= 0) || (eN + 8 < eP);
+  }
+  if (direct) {
+    CAcc<K, C> ca;
+    cacc_zero(ca);
+    for (int i = c + lane; i < n; i += 32) {
+      cmd<K, C> v;
+      ld(y, n, i, v);
+      acc_fma(ca.re, v.re, v.re);
+      if constexpr (C == 2) acc_fma(ca.re, v.im, v.im);
+    }
+    cmd<K, C> t;
+    warp_sum_acc(ca, t);
+    md_copy(t.re, N);
+  }
+  const bool singular = !nonzero(N[0]);
+  if (singular) N[0] = 1.0;  // keep the arithmetic finite; reported below
   double ry[K], alpha[K];
-  md_rsqrt(nrm.re, ry);
-  md_mul(nrm.re, ry, alpha);
+  md_rsqrt(N, ry);  // 1 / |x_c|
+  md_mul(N, ry, alpha);
   cmd<K, C> x0;
-  ld(p.Rm, p.Nnn, (long long)j * n + j, x0);
+  ld(y, n, c, x0);
   double ax0[K];
   cmd<K, C> sg;
   cmd_zero(sg);
@@ -453,9 +538,9 @@ __device__ void qr_reflector(const QrParams& p, int j, unsigned ep) {
     cmd_abs2(x0, a2x);
     const bool z = !nonzero(a2x[0]);
     if (z) a2x[0] = 1.0;
-    md_rsqrt(a2x, rx);            // 1/|x0|
-    md_mul(a2x, rx, ax0);         // |x0|
-    md_mul(x0.re, rx, sg.re);     // s = x0 / |x0|
+    md_rsqrt(a2x, rx);
+    md_mul(a2x, rx, ax0);
+    md_mul(x0.re, rx, sg.re);
     md_mul(x0.im, rx, sg.im);
     if (z) {
       md_zero(ax0);
@@ -466,108 +551,137 @@ __device__ void qr_reflector(const QrParams& p, int j, unsigned ep) {
   cmd<K, C> salpha, v0;
   cmd_scale(sg, alpha, salpha);
   cmd_add(x0, salpha, v0);
-  // tau = 2 / v^H v = 1 / (N + alpha |x0|)
   double t1[K], t2[K], tau[K];
   md_mul(alpha, ax0, t1);
-  md_add(nrm.re, t1, t2);
+  md_add(N, t1, t2);
   md_recip(t2, tau);
   if (singular) {
     md_zero(tau);
     if (lane == 0) atomicOr(p.status, MDN_DEV_SINGULAR);
   }
-  // reflector, R_jj = -s alpha, zeros below the diagonal
-  for (int i = j + lane; i < n; i += 32) {
-    cmd<K, C> x;
-    if (i == j) {
-      st(p.Vm, p.Nnn, (long long)i * n + j, v0);
-      cmd<K, C> r;
-      md_neg(salpha.re, r.re);
-      md_neg(salpha.im, r.im);
-      st(p.Rm, p.Nnn, (long long)i * n + j, r);
-    } else {
-      ld(p.Rm, p.Nnn, (long long)i * n + j, x);
-      st(p.Vm, p.Nnn, (long long)i * n + j, x);
-      cmd_zero(x);
-      st(p.Rm, p.Nnn, (long long)i * n + j, x);
-    }
+  if (lane == 0) {
+    st(p.salpha, p.n, c, salpha);
+    st(p.v0, p.n, c, v0);
+    st_real(p.tau, p.n, c, tau);
+    cmd<K, C> r;
+    md_neg(salpha.re, r.re);
+    md_neg(salpha.im, r.im);
+    st(p.Rm, p.Nnn, (long long)c * n + c, r);
   }
-  if (lane == 0) st_real(p.tau, p.n, j, tau);
-  warp_publish(&p.flags[j], ep);
-  // 1 / R_jj = -conj(s) / alpha (|s| = 1), published separately
-  double ra[K];
-  md_recip(alpha, ra);
+  warp_publish(&fref[c], ep);
+  // 1 / R_cc = -conj(s) / |x_c|
   cmd<K, C> rinv;
-  md_neg(ra, ra);
-  md_mul(sg.re, ra, rinv.re);
-  if constexpr (C == 2) {
-    double nra[K];
-    md_neg(ra, nra);
-    md_mul(sg.im, nra, rinv.im);
-  } else {
-    md_zero(rinv.im);
-  }
+  double nry[K];
+  md_neg(ry, nry);
+  md_mul(sg.re, nry, rinv.re);
+  if constexpr (C == 2) md_mul(sg.im, ry, rinv.im);
+  else md_zero(rinv.im);
   if (singular) cmd_zero(rinv);
-  if (lane == 0) st(p.rinv, p.n, j, rinv);
-  warp_publish(&p.flags[p.n + j], ep);
+  if (lane == 0) st(p.rinv, p.n, c, rinv);
+  warp_publish(&frinv[c], ep);
+}
+
+// Identity warp e: Q^H e_e as the reflectors appear (column e of Y = Q^H).
+template <int K, int C>
+__device__ void qr_identity(const QrParams& p, int e, double* y, unsigned ep) {
+  const int lane = threadIdx.x & 31;
+  const int n = p.n;
+  unsigned* fref = p.flags + n;
+  for (int i = lane; i < n; i += 32) {
+    cmd<K, C> v;
+    cmd_zero(v);
+    if (i == e) v.re[0] = 1.0;
+    st(y, n, i, v);
+  }
+  __syncwarp();
+  for (int j = 0; j < n; ++j) {
+    if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
+    cmd<K, C> dot;
+    double dummy[K];
+    qr_lookahead<K, C>(p, j, y, false, dot, dummy);
+    qr_apply_la<K, C>(p, j, y, dot);
+  }
+  for (int i = lane; i < n; i += 32) {
+    cmd<K, C> v;
+    ld(y, n, i, v);
+    st(p.Y, p.Nnn, (long long)i * n + e, v);
+  }
+}
+
+// Row warp i of Z = R^{-1}, built column by column as R grows:
+//   Z[i][i] = 1/R_ii,  Z[i][c] = -(1/R_cc) sum_{k=i..c-1} Z[i][k] R[k][c]  (c > i),
+// the block inverse of the leading (c+1) x (c+1) part of R.
+template <int K, int C>
+__device__ void qr_rinv_row(const QrParams& p, int i, double* z, unsigned ep) {
+  const int lane = threadIdx.x & 31;
+  const int n = p.n;
+  unsigned* frinv = p.flags + 2 * n;
+  for (int c = i; c < n; ++c) {
+    if (!warp_wait(&frinv[c], ep, p.spin_limit, p.status)) return;
+    cmd<K, C> rc;
+    ld(p.rinv, p.n, c, rc);
+    cmd<K, C> zc;
+    if (c == i) {
+      zc = rc;
+    } else {
+      CAcc<K, C> acc;
+      cacc_zero(acc);
+      for (int k = i + lane; k < c; k += 32) {
+        cmd<K, C> zk, rk;
+        ld(z, n, k, zk);
+        ld(p.Rm, p.Nnn, (long long)k * n + c, rk);
+        cacc_fma(acc, zk, rk);
+      }
+      cmd<K, C> s, t;
+      warp_sum_acc(acc, s);
+      cmd_mul(s, rc, t);
+      md_neg(t.re, zc.re);
+      md_neg(t.im, zc.im);
+    }
+    if (lane == 0) {
+      st(z, n, c, zc);
+      st(p.Z, p.Nnn, (long long)i * n + c, zc);
+    }
+    __syncwarp();
+  }
 }
 
 template <int K, int C>
 __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrParams p) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n = p.n;
+  extern __shared__ __align__(16) unsigned char qr_smem[];
+  const int warp = threadIdx.x >> 5;
   const unsigned ep = *p.epoch;
-  const bool colwarp = blockIdx.x < p.nA;
-  const int c = (colwarp ? blockIdx.x : blockIdx.x - p.nA) * (QR_THREADS / 32) + warp;
-  if (c >= n) return;
-  if (colwarp) {
-    // my column of A0 -> Rm
-    for (int i = lane; i < n; i += 32) {
-      cmd<K, C> v;
-      ld(p.A0, p.NA, (long long)i * n + c, v);
-      st(p.Rm, p.Nnn, (long long)i * n + c, v);
+  double* y = reinterpret_cast<double*>(qr_smem) + (size_t)warp * p.n * 2 * K;
+  const int role = blockIdx.x / p.nA;
+  const int c = (blockIdx.x - role * p.nA) * (QR_THREADS / 32) + warp;
+  if (c >= p.n) return;
+  if (role == 0) qr_column<K, C>(p, c, y, ep);
+  else if (role == 1) qr_identity<K, C>(p, c, y, ep);
+  else qr_rinv_row<K, C>(p, c, y, ep);
+}
+
+// W = Z Y = R^{-1} Q^H: one warp per entry, lanes over k >= i (Z is upper
+// triangular), over the whole GPU.
+template <int K, int C>
+__global__ void w_kernel(QrParams p) {
+  const int n = p.n;
+  const int lane = threadIdx.x & 31;
+  const long long nn = (long long)n * n;
+  const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = wid; t < nn; t += nw) {
+    const int i = (int)(t / n), e = (int)(t - (long long)i * n);
+    CAcc<K, C> acc;
+    cacc_zero(acc);
+    for (int k = i + lane; k < n; k += 32) {
+      cmd<K, C> z, yv;
+      ld(p.Z, p.Nnn, (long long)i * n + k, z);
+      ld(p.Y, p.Nnn, (long long)k * n + e, yv);
+      cacc_fma(acc, z, yv);
     }
-    __syncwarp();
-    for (int j = 0; j < c; ++j) {
-      if (!warp_wait(&p.flags[j], ep, p.spin_limit, p.status)) return;
-      qr_apply<K, C>(p, j, p.Rm, p.Nnn, c);
-    }
-    qr_reflector<K, C>(p, c, ep);
-  } else {
-    // column c of the identity -> Q^H e_c -> R^{-1} Q^H e_c
-    for (int i = lane; i < n; i += 32) {
-      cmd<K, C> v;
-      cmd_zero(v);
-      if (i == c) v.re[0] = 1.0;
-      st(p.Y, p.Nnn, (long long)i * n + c, v);
-    }
-    __syncwarp();
-    for (int j = 0; j < n; ++j) {
-      if (!warp_wait(&p.flags[j], ep, p.spin_limit, p.status)) return;
-      qr_apply<K, C>(p, j, p.Y, p.Nnn, c);
-    }
-    // column-oriented back substitution: x_i = y_i / R_ii, y_k -= R_ki x_i
-    for (int i = n - 1; i >= 0; --i) {
-      if (!warp_wait(&p.flags[n + i], ep, p.spin_limit, p.status)) return;
-      cmd<K, C> yi, ri, xi;
-      ld(p.Y, p.Nnn, (long long)i * n + c, yi);
-      ld(p.rinv, p.n, i, ri);
-      cmd_mul(yi, ri, xi);
-      if (lane == 0) st(p.W, p.Nnn, (long long)i * n + c, xi);
-      cmd<K, C> nx;
-      md_neg(xi.re, nx.re);
-      md_neg(xi.im, nx.im);
-      for (int k = lane; k < i; k += 32) {
-        cmd<K, C> rk, yk;
-        ld(p.Rm, p.Nnn, (long long)k * n + i, rk);
-        ld(p.Y, p.Nnn, (long long)k * n + c, yk);
-        CAcc<K, C> a;
-        cacc_set(a, yk);
-        cacc_fma(a, nx, rk);
-        cacc_get(a, yk);
-        st(p.Y, p.Nnn, (long long)k * n + c, yk);
-      }
-      __syncwarp();
-    }
+    cmd<K, C> w;
+    warp_sum_acc(acc, w);
+    if (lane == 0) st(p.W, p.Nnn, t, w);
   }
 }
 
@@ -782,8 +896,11 @@ cudaError_t launch_qr(const QrParams& p, cudaStream_t s) {
   }
   QrParams q = p;
   void* args[] = {(void*)&q};
-  return cudaLaunchCooperativeKernel((const void*)qr_kernel<K, C>, dim3(2 * p.nA), dim3(QR_THREADS), args,
-                                     QR_SMEM_RESERVE, s);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)qr_kernel<K, C>, dim3(3 * p.nA), dim3(QR_THREADS), args,
+                                              QR_SMEM_RESERVE, s);
+  if (e != cudaSuccess) return e;
+  w_kernel<K, C><<<grid_for((long long)p.n * p.n * 32, 128), 128, 0, s>>>(q);
+  return cudaGetLastError();
 }
 template <int K, int C>
 cudaError_t launch_fsub(const FsubParams& p, cudaStream_t s) {

@@ -314,35 +314,82 @@ __device__ __forceinline__ void md_mul_d(const double (&a)[K], double d, double 
   md_mul(a, b, r);
 }
 
-// One Newton step for y ~ 1/b at KK limbs: y <- y + y (1 - b y).  Each step
-// doubles the number of correct bits, so the precision grows 53 -> 106 ->
-// 212 -> 424 bits with KK = 2, 4, 8 (Karp and Markstein, "High-precision
-// division and square root", ACM TOMS 1997).
-template <int KK, int K>
-__device__ __forceinline__ void recip_step(const double (&b)[K], double (&y)[K]) {
-  double bb[KK], yy[KK], t[KK], e[KK], one[KK];
+// Term t of level L (a runtime value that is constant after unrolling).
+template <int K>
+__device__ __forceinline__ void cascade_at(Acc<K>& a, int L, double t) {
 #pragma unroll
-  for (int l = 0; l < KK; ++l) {
-    bb[l] = b[l];
-    yy[l] = y[l];
-    one[l] = 0.0;
-  }
-  one[0] = 1.0;
-  md_mul(bb, yy, t);
-  md_sub(one, t, e);
-  md_mul(yy, e, t);
-  md_add(yy, t, yy);
-#pragma unroll
-  for (int l = 0; l < KK; ++l) y[l] = yy[l];
+  for (int m = 0; m < K - 1; ++m)
+    if (m >= L) two_sum(a.l[m], t, a.l[m], t);
+  a.l[K - 1] = __dadd_rn(a.l[K - 1], t);
 }
-// y = 1 / b
+
+// r = x * y for y with KB <= K limbs (the partial products x_i y_j, j < KB,
+// in the same level scheme as md_mul).
+template <int K, int KB>
+__device__ __forceinline__ void md_mul_part(const double (&x)[K], const double (&y)[KB], double (&r)[K]) {
+  if constexpr (KB == K) {
+    md_mul(x, y, r);
+  } else {
+    Acc<K> a;
+    double lo[K];
+#pragma unroll
+    for (int L = 0; L < K; ++L) {  // seeds: x_L y_0 at level L
+      if (L <= K - 2) two_prod(x[L], y[0], a.l[L], lo[L]);
+      else a.l[K - 1] = __dmul_rn(x[K - 1], y[0]);
+    }
+#pragma unroll
+    for (int L = 0; L <= K - 2; ++L) cascade_at(a, L + 1, lo[L]);
+#pragma unroll
+    for (int j = 1; j < KB; ++j)
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int L = i + j;
+        if (L > K) continue;
+        if (L <= K - 2) {
+          double p, e;
+          two_prod(x[i], y[j], p, e);
+          cascade_at(a, L, p);
+          cascade_at(a, L + 1, e);
+        } else {
+          a.l[K - 1] = __fma_rn(x[i], y[j], a.l[K - 1]);
+        }
+      }
+    acc_get(a, r);
+  }
+}
+
+// y = 1 / b: the reciprocal at K/2 limbs, then one Newton correction
+// y = y_h + y_h (1 - b y_h) whose residual is formed at K limbs and whose
+// product is formed at K/2 limbs (the residual is ~2^(-53 K/2)), after
+// Karp and Markstein ("High-precision division and square root", ACM TOMS
+// 1997).  Seed: the correctly rounded double reciprocal.
 template <int K>
 __device__ __forceinline__ void md_recip(const double (&b)[K], double (&y)[K]) {
-  md_zero(y);
-  y[0] = __drcp_rn(b[0]);
-  if constexpr (K >= 2) recip_step<2, K>(b, y);
-  if constexpr (K >= 4) recip_step<4, K>(b, y);
-  if constexpr (K >= 8) recip_step<8, K>(b, y);
+  if constexpr (K == 1) {
+    y[0] = __drcp_rn(b[0]);
+  } else {
+    constexpr int H = K / 2;
+    double bh[H], yh[H];
+#pragma unroll
+    for (int l = 0; l < H; ++l) bh[l] = b[l];
+    md_recip<H>(bh, yh);
+    double p[K], one[K], e[K];
+    md_mul_part<K, H>(b, yh, p);
+    md_zero(one);
+    one[0] = 1.0;
+    md_sub(one, p, e);
+    double eh[H], corr[H];
+#pragma unroll
+    for (int l = 0; l < H; ++l) eh[l] = e[l];
+    md_mul<H>(yh, eh, corr);
+    double t[K];
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+      t[l] = yh[l];
+      t[H + l] = corr[l];
+    }
+    renorm<K, K>(t, y);
+  }
 }
 // r = a / b = a * (1/b)
 template <int K>
@@ -352,35 +399,35 @@ __device__ __forceinline__ void md_div(const double (&a)[K], const double (&b)[K
   md_mul(a, y, r);
 }
 
-// One Newton step for y ~ 1/sqrt(a) at KK limbs: y <- y + y (1 - a y^2) / 2.
-template <int KK, int K>
-__device__ __forceinline__ void rsqrt_step(const double (&a)[K], double (&y)[K]) {
-  double aa[KK], yy[KK], t[KK], e[KK], one[KK];
-#pragma unroll
-  for (int l = 0; l < KK; ++l) {
-    aa[l] = a[l];
-    yy[l] = y[l];
-    one[l] = 0.0;
-  }
-  one[0] = 1.0;
-  md_mul(yy, yy, t);
-  md_mul(aa, t, e);
-  md_sub(one, e, t);
-  md_mul(yy, t, e);
-#pragma unroll
-  for (int l = 0; l < KK; ++l) e[l] = 0.5 * e[l];  // exact
-  md_add(yy, e, yy);
-#pragma unroll
-  for (int l = 0; l < KK; ++l) y[l] = yy[l];
-}
-// y = 1 / sqrt(a), a > 0
+// y = 1 / sqrt(a), a > 0: the same scheme with y = y_h + y_h (1 - a y_h^2) / 2.
 template <int K>
 __device__ __forceinline__ void md_rsqrt(const double (&a)[K], double (&y)[K]) {
-  md_zero(y);
-  y[0] = __drcp_rn(__dsqrt_rn(a[0]));
-  if constexpr (K >= 2) rsqrt_step<2, K>(a, y);
-  if constexpr (K >= 4) rsqrt_step<4, K>(a, y);
-  if constexpr (K >= 8) rsqrt_step<8, K>(a, y);
+  if constexpr (K == 1) {
+    y[0] = __drcp_rn(__dsqrt_rn(a[0]));
+  } else {
+    constexpr int H = K / 2;
+    double ah[H], yh[H];
+#pragma unroll
+    for (int l = 0; l < H; ++l) ah[l] = a[l];
+    md_rsqrt<H>(ah, yh);
+    double q[K], p[K], one[K], e[K];
+    md_mul_part<K, H>(a, yh, q);
+    md_mul_part<K, H>(q, yh, p);
+    md_zero(one);
+    one[0] = 1.0;
+    md_sub(one, p, e);
+    double eh[H], corr[H];
+#pragma unroll
+    for (int l = 0; l < H; ++l) eh[l] = 0.5 * e[l];  // exact
+    md_mul<H>(yh, eh, corr);
+    double t[K];
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+      t[l] = yh[l];
+      t[H + l] = corr[l];
+    }
+    renorm<K, K>(t, y);
+  }
 }
 // r = sqrt(a) = a / sqrt(a) for a > 0, r = 0 for a = 0
 template <int K>

@@ -81,17 +81,20 @@ struct AsmParams {
 };
 
 struct QrParams {
-  int n, nA;
+  int n, nA;  // nA blocks per role: columns of A0, columns of the identity, rows of R^{-1}
   const double* A0;
   long long NA;   // stride of the A array the A0 slice lives in
   long long Nnn;  // n*n
   double* Rm;
   double* Vm;
-  double* Y;
+  double* Y;  // Q^H (identity columns under all reflectors)
+  double* Z;  // R^{-1}
   double* W;
-  double* tau;   // [K][n]
-  double* rinv;  // [K][C][n]
-  unsigned* flags;  // [2n]
+  double* tau;     // [K][n]
+  double* rinv;    // [K][C][n]
+  double* salpha;  // [K][C][n] s_j |x_j| (R_jj = -salpha_j)
+  double* v0;      // [K][C][n] leading entry of reflector j
+  unsigned* flags;  // [3n]: column published, reflector published, 1/R_jj published
   const unsigned* epoch;
   int* status;
   long long spin_limit;  // nanoseconds a flag wait may last
@@ -143,7 +146,7 @@ struct KernelTable {
   cudaError_t (*a0)(const A0Params&, cudaStream_t);
   int (*ed_blocks_per_sm)();
   cudaError_t (*assemble)(const AsmParams&, bool want_A, cudaStream_t);
-  cudaError_t (*qr)(const QrParams&, cudaStream_t);
+  cudaError_t (*qr)(const QrParams&, cudaStream_t);  // QR, Q^H, R^{-1}, then W = R^{-1} Q^H
   cudaError_t (*fsub)(const FsubParams&, cudaStream_t);
   cudaError_t (*update)(const UpdParams&, cudaStream_t);
 };

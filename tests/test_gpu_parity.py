@@ -103,6 +103,23 @@ def test_solve_matches_oracle(md, K, C, n, d):
     assert np.max(mt.series_rel_error(to_np(dx), dx_ref)) <= TOL[K]
 
 
+@pytest.mark.parametrize("K,C", [(2, 1), (4, 1), (8, 1), (2, 2), (4, 2), (8, 2)])
+def test_series_division_n1(md, K, C):
+    """n = 1: the block Toeplitz solve is the series quotient b(t) / a(t);
+    it exercises the 1x1 reflector, 1/R and the reciprocal and square root
+    kernels at full precision over 64 coefficients."""
+    D = 64
+    A = wl.random_md((D, 1, 1), K, C, 900 + K + C, unit_circle=(C == 2))
+    A[0, 0, 0] += 2.0 if C == 1 else 0.0
+    A[:, :, 1:] *= (0.25 ** np.arange(1, D))[:, None, None]  # no zero of a(t) near the unit disk
+    b = wl.random_md((1, D), K, C, 901 + K)
+    dx_ref = oracle.solve(A, b)
+    cfg = wl.small_config(K, C, n=1, d=D - 1, mono_per_eq=1, kmin=1, kmax=1, index=806)
+    s, _, _ = planted(cfg, with_cst=False)
+    dx = _newton(md, s).solve(A, b)
+    assert np.max(mt.series_rel_error(to_np(dx), dx_ref)) <= TOL[K]
+
+
 def test_singular_A0_is_reported(md):
     K, C, n, d = 2, 1, 4, 3
     A = wl.random_md((d + 1, n, n), K, C, 3)

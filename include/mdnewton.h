@@ -66,7 +66,8 @@ typedef enum {
   MDN_ENOTCONVERGED = 5,   /* tolerance not met within max_steps; x readable */
   MDN_ETIMEOUT = 6,        /* a bounded device wait gave up */
   MDN_ESTATE = 7,          /* call out of order (no system or series loaded) */
-  MDN_EWORKSPACE = 8       /* workspace smaller than mdn_workspace_bytes() */
+  MDN_EWORKSPACE = 8,      /* workspace smaller than mdn_workspace_bytes() */
+  MDN_ETOOLARGE = 9        /* sizes beyond MDN_STATIC_SCRATCH_BYTES (mdn_evaluate_static) */
 } mdn_status;
 
 /* Most Newton steps one mdn_newton() call may run (size of the device history). */
@@ -154,6 +155,32 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
  * accumulated milliseconds (ms_out) and kernel launch counts (launches_out)
  * per phase into host arrays of MDN_NUM_PHASES entries (either may be NULL). */
 mdn_status mdn_profile(mdn_ctx* ctx, int enable, double* ms_out, int64_t* launches_out);
+
+/* Size of the static device scratch of mdn_evaluate_static(). */
+#define MDN_STATIC_SCRATCH_BYTES (2u << 20)
+
+/* f(x(t)) without a context, a workspace or any device allocation.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory (code running while a CUDA graph is captured,
+ * plug-ins inside an application that owns the device allocator, loops that
+ * must not allocate after start-up).  The scratch of the evaluation lives in
+ * one file-scope device array of MDN_STATIC_SCRATCH_BYTES that every GPU
+ * loading the library keeps until the process exits.
+ *   All pointers are device pointers in the layouts above: eq_of_monomial [M],
+ *   var_ptr [M+1], var_idx [n_var_refs], coeff [K][C][M][d+1], const_term and
+ *   x [K][C][n][d+1]; f_out receives [K][C][n][d+1].
+ * The call looks up the array's device address on its first use on a device
+ * (cudaGetSymbolAddress, with that device current), so that first call should
+ * come before any stream capture.  It returns MDN_ETOOLARGE when
+ * 8 * (32 + n * 2 * K * C * (d+1)) bytes exceed MDN_STATIC_SCRATCH_BYTES,
+ * MDN_EINVAL for bad sizes or an index out of range (checked on the device),
+ * and synchronises the stream to read that check.  All calls share the array
+ * and it keeps the last call's contents: calls whose kernels overlap on the
+ * GPU race.  No cudaMalloc, cudaFree or allocating routine is called. */
+mdn_status mdn_evaluate_static(int limbs, int is_complex, int n, int degree, int n_monomials, int n_var_refs,
+                               const int32_t* eq_of_monomial, const int32_t* var_ptr, const int32_t* var_idx,
+                               const double* coeff, const double* const_term, const double* x, double* f_out,
+                               void* cuda_stream);
 
 /* Synchronise the context's stream and return the device status as an
  * mdn_status (MDN_OK when no device condition was raised). */

@@ -21,15 +21,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "_build", f"libmdnewton-{platform.machine()}.so")
 
 STATUS = {0: "MDN_OK", 1: "MDN_EINVAL", 2: "MDN_ECUDA", 3: "MDN_ESINGULAR", 4: "MDN_ENONFINITE",
-          5: "MDN_ENOTCONVERGED", 6: "MDN_ETIMEOUT", 7: "MDN_ESTATE", 8: "MDN_EWORKSPACE"}
+          5: "MDN_ENOTCONVERGED", 6: "MDN_ETIMEOUT", 7: "MDN_ESTATE", 8: "MDN_EWORKSPACE", 9: "MDN_ETOOLARGE"}
 MDN_OK, MDN_EINVAL, MDN_ECUDA, MDN_ESINGULAR, MDN_ENONFINITE, MDN_ENOTCONVERGED, MDN_ETIMEOUT, \
-    MDN_ESTATE, MDN_EWORKSPACE = range(9)
+    MDN_ESTATE, MDN_EWORKSPACE, MDN_ETOOLARGE = range(10)
+MDN_STATIC_SCRATCH_BYTES = 2 << 20
 MDN_MAX_STEPS = 64
 MDN_MAX_DEGREE = 63
 
 EXPORTS = ("mdn_create", "mdn_workspace_bytes", "mdn_load_system", "mdn_set_series", "mdn_newton",
            "mdn_get_series", "mdn_get_residual", "mdn_evaluate", "mdn_solve", "mdn_profile",
-           "mdn_status_word", "mdn_last_error", "mdn_destroy")
+           "mdn_status_word", "mdn_last_error", "mdn_destroy", "mdn_evaluate_static")
 MDN_NUM_PHASES = 5
 PHASES = ("evaluate", "assemble", "qr", "forward", "update")
 
@@ -64,6 +65,7 @@ def load(path: str = None) -> ctypes.CDLL:
     L.mdn_solve.argtypes = [P, P, P, P]
     L.mdn_profile.argtypes = [P, I, P, P]
     L.mdn_status_word.argtypes = [P]
+    L.mdn_evaluate_static.argtypes = [I, I, I, I, I, I, P, P, P, P, P, P, P, P]
     L.mdn_last_error.argtypes = [P]
     L.mdn_last_error.restype = ctypes.c_char_p
     L.mdn_destroy.argtypes = [P]
@@ -156,6 +158,20 @@ def mdn_profile(ctx, enable: int):
     st = load().mdn_profile(ctx, int(enable), ms.ctypes.data_as(ctypes.c_void_p),
                             launches.ctypes.data_as(ctypes.c_void_p))
     return st, ms, launches
+
+
+def mdn_evaluate_static(limbs, is_complex, n, degree, n_monomials, n_var_refs, eq_of_monomial, var_ptr, var_idx,
+                        coeff, const_term, x, f_out, cuda_stream) -> int:
+    """f(x(t)) with no context and no device allocation (device int32
+    structure tensors, device float64 series); see include/mdnewton.h."""
+    for t in (eq_of_monomial, var_ptr, var_idx):
+        if not t.is_cuda or str(t.dtype) != "torch.int32" or not t.is_contiguous():
+            raise TypeError("expected contiguous int32 CUDA tensors for the structure")
+    return load().mdn_evaluate_static(int(limbs), int(is_complex), int(n), int(degree), int(n_monomials),
+                                      int(n_var_refs), ctypes.c_void_p(eq_of_monomial.data_ptr()),
+                                      ctypes.c_void_p(var_ptr.data_ptr()), ctypes.c_void_p(var_idx.data_ptr()),
+                                      _ptr(coeff), _ptr(const_term), _ptr(x), _ptr(f_out),
+                                      ctypes.c_void_p(int(cuda_stream)))
 
 
 def mdn_status_word(ctx) -> int:

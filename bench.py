@@ -5,8 +5,10 @@ Workload (default): quad double, real, n = 64 equations and unknowns,
 16 monomials of 2..8 distinct variables per equation plus 64 x_i, series of
 degree d = 31, planted solution; one "step" is one Newton step (evaluation
 and differentiation, Householder QR of A0 and its inverse, forward
-substitution over the 32 coefficient blocks, update and norms).  Every group
-of 7 steps restarts from the start series, the config's step count.
+substitution over the 32 coefficient blocks, update and norms).  The timed
+steps run as solves of 7 steps (the workload's step count) from the start
+series, one mdn_newton call each, with CUDA events around every solve and
+the L2 flushed between solves.
 
 Output: one JSON line (rank 0).  ``value`` is Newton steps/s over all ranks
 from CUDA events around each timed step (inputs resident in HBM, L2 flushed
@@ -163,7 +165,8 @@ def config_dict(cfg, args):
     return {"workload": cfg.name, "limbs": cfg.K, "complex": cfg.C == 2, "n": cfg.n, "degree": cfg.d,
             "monomials_per_equation": cfg.mono_per_eq, "vars_per_monomial": [cfg.kmin, cfg.kmax],
             "newton_steps_per_solve": cfg.steps, "parallelism": f"replicas x{args.gpus}",
-            "l2": "flushed between timed steps (256 MiB write)"}
+            "l2": "flushed between timed solves (256 MiB write); steps run in solves of "
+                  f"{cfg.steps} from the start series"}
 
 
 # ---------------------------------------------------------------------------
@@ -196,15 +199,23 @@ def run_ours(args, cfg):
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(local)
 
-    def one_step(i):
-        if i % cfg.steps == 0:
-            nw.set_series(x0_dev)
-        st, done, _ = md.mdn_newton(nw.ctx, 1, 0.0)
-        if st != md.MDN_OK:
+    def solve_chunks(total):
+        # Newton steps in solves of cfg.steps from the start series (the last
+        # one shorter); each solve is one mdn_newton call
+        out, left = [], total
+        while left > 0:
+            out.append(min(cfg.steps, left))
+            left -= out[-1]
+        return out
+
+    def run_solve(nsteps):
+        nw.set_series(x0_dev)
+        st, done, _ = md.mdn_newton(nw.ctx, nsteps, 0.0)
+        if st != md.MDN_OK or done != nsteps:
             raise md.MdnError(st, md.mdn_last_error(nw.ctx))
 
-    for i in range(args.warmup):
-        one_step(i)
+    for c in solve_chunks(args.warmup):
+        run_solve(c)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -212,12 +223,12 @@ def run_ours(args, cfg):
     md.mdn_profile(nw.ctx, 1)
     evs = []
     t_wall = time.perf_counter()
-    for i in range(args.steps):
+    for c in solve_chunks(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        one_step(i)
+        run_solve(c)
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()

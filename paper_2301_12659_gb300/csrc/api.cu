@@ -166,7 +166,7 @@ struct Layout {
   size_t total = 0;
   size_t o_order, o_mono_k, o_mono_vp, o_mono_sbase, o_vidx, o_sched, o_sched_off, o_sched_nw, o_eq_ptr,
       o_eq_mon, o_pair_ptr, o_pair_slot, o_occ, o_counter, o_status, o_flags, o_epoch, o_done;
-  size_t o_x, o_f, o_dx, o_r, o_out, o_out0, o_scratch, o_A, o_Rm, o_Vm, o_Y, o_Z, o_W, o_tau, o_rinv, o_salpha, o_v0, o_fabs, o_dxabs,
+  size_t o_x, o_f, o_dx, o_r, o_out, o_out0, o_scratch, o_A, o_A0b, o_Rm, o_Vm, o_Y, o_Z, o_W, o_xn0, o_tau, o_rinv, o_salpha, o_v0, o_fabs, o_dxabs,
       o_resabs, o_hist;
 };
 
@@ -365,11 +365,13 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_out0 = take(8 * KC * (size_t)ctx->S);
   L.o_scratch = take(8 * KC * (size_t)ctx->Wtot * ctx->Smax * D);
   L.o_A = take(8 * KC * D * n * n);
+  L.o_A0b = take(8 * KC * n * n * 2);  // A_0 of this step and of the next (pipelined QR)
   L.o_Rm = take(8 * KC * n * n);
   L.o_Vm = take(8 * KC * n * n);
   L.o_Y = take(8 * KC * n * n);
   L.o_Z = take(8 * KC * n * n);
-  L.o_W = take(8 * KC * n * n);
+  L.o_W = take(8 * KC * n * n * 2);    // A_0^{-1} of this step and of the next
+  L.o_xn0 = take(8 * KC * n);          // constant coefficients of the next series
   L.o_tau = take(8 * (size_t)ctx->K * n);
   L.o_rinv = take(8 * KC * n);
   L.o_salpha = take(8 * KC * n);
@@ -503,15 +505,20 @@ mdn_status mdn_get_series(const mdn_ctx* cctx, double* x_out) {
 // ---- launch sequences -------------------------------------------------------
 
 // A_0 = J(x_0) into the j = 0 slice of A (constant coefficients only).
-static mdn_status run_a0(mdn_ctx* ctx, const double* x, double* A, cudaStream_t st) {
+// x: constant coefficients every xstride doubles in limb arrays of Nx doubles;
+// A_0 is written with limb stride NA (n*n for a separate matrix, D*n*n for
+// the j = 0 slice of a Jacobian series).
+static mdn_status run_a0(mdn_ctx* ctx, const double* x, long long Nx, int xstride, double* A, long long NA,
+                         cudaStream_t st) {
   const Layout& L = ctx->L;
-  const long long D = ctx->D, n = ctx->n;
+  const long long D = ctx->D;
   A0Params a{};
   a.n = ctx->n;
   a.D = ctx->D;
   a.M = ctx->M;
   a.x = x;
-  a.Nx = n * D;
+  a.Nx = Nx;
+  a.xstride = xstride;
   a.coeff = ctx->coeff;
   a.Nc = (long long)ctx->M * D;
   a.mono_k = ctx->at<int>(L.o_mono_k);
@@ -525,7 +532,7 @@ static mdn_status run_a0(mdn_ctx* ctx, const double* x, double* A, cudaStream_t 
   a.pair_ptr = ctx->at<int>(L.o_pair_ptr);
   a.pair_slot = ctx->at<int>(L.o_pair_slot);
   a.A = A;
-  a.NA = D * n * n;
+  a.NA = NA;
   CU(ctx->kt->a0(a, st));
   return MDN_OK;
 }
@@ -589,22 +596,22 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
 }
 
 // Householder QR of A0 (the j = 0 slice of A) and W = A0^{-1} on stream st.
-static mdn_status run_qr(mdn_ctx* ctx, const double* A, cudaStream_t st) {
+static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* W, cudaStream_t st) {
   const Layout& L = ctx->L;
-  const long long D = ctx->D, n = ctx->n;
+  const long long n = ctx->n;
   bump_kernel<<<1, 1, 0, st>>>(ctx->at<unsigned>(L.o_epoch));
   CU(cudaGetLastError());
   QrParams q{};
   q.n = ctx->n;
   q.nA = (ctx->n + (QR_THREADS / 32) - 1) / (QR_THREADS / 32);
-  q.A0 = A;
-  q.NA = D * n * n;
+  q.A0 = A0;
+  q.NA = NA0;
   q.Nnn = n * n;
   q.Rm = ctx->at<double>(L.o_Rm);
   q.Vm = ctx->at<double>(L.o_Vm);
   q.Y = ctx->at<double>(L.o_Y);
   q.Z = ctx->at<double>(L.o_Z);
-  q.W = ctx->at<double>(L.o_W);
+  q.W = W;
   q.tau = ctx->at<double>(L.o_tau);
   q.rinv = ctx->at<double>(L.o_rinv);
   q.salpha = ctx->at<double>(L.o_salpha);
@@ -619,8 +626,12 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A, cudaStream_t st) {
 
 static int qr_blocks(const mdn_ctx* ctx) { return 3 * ((ctx->n + (QR_THREADS / 32) - 1) / (QR_THREADS / 32)); }
 
-// Forward substitution for dx with right hand side sgn * rhs (needs W).
-static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* rhs, int sgn, double* dx) {
+// Forward substitution for dx with right hand side sgn * rhs: stage 0 alone
+// (dx_0 = W r_0, and x_0 + dx_0 into the xnext0 buffer when x is given), the
+// event e0 recorded after it when not null, then the remaining stages on
+// `blocks` SMs.
+static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, long long NA0, const double* W,
+                              const double* rhs, int sgn, double* dx, const double* x, cudaEvent_t e0, int blocks) {
   const Layout& L = ctx->L;
   const long long D = ctx->D, n = ctx->n;
   ph_begin(ctx, MDN_PHASE_FORWARD);
@@ -628,76 +639,124 @@ static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* rhs, 
   u.n = ctx->n;
   u.D = ctx->D;
   u.rhs_sign = sgn;
+  u.first_stage = 1;
   u.nW = std::min(ctx->n, 4 * FSUB_WBLOCKS);
-  u.nOwn = (int)std::min<long long>(4LL * std::max(1, ctx->num_sms - FSUB_WBLOCKS), (long long)ctx->n * ctx->D);
+  const int wb = (u.nW + 3) / 4;
+  u.nOwn = (int)std::min<long long>(4LL * std::max(1, blocks - wb), (long long)ctx->n * ctx->D);
   u.A = A;
   u.NA = D * n * n;
-  u.W = ctx->at<double>(L.o_W);
+  u.A0 = A0;
+  u.NA0 = NA0;
+  u.W = W;
   u.Nnn = n * n;
   u.rhs = rhs;
   u.r = ctx->at<double>(L.o_r);
   u.dx = dx;
   u.Nx = n * D;
+  u.x = x;
+  u.xnext0 = x ? ctx->at<double>(L.o_xn0) : nullptr;
   u.resabs = ctx->at<double>(L.o_resabs);
   u.rdone = ctx->at<unsigned>(L.o_done);
   u.xdone = u.rdone + ctx->D;
   u.status = ctx->at<int>(L.o_status);
   u.spin_limit = SPIN_LIMIT;
   CU(cudaMemsetAsync(u.rdone, 0, 4 * 2 * (size_t)ctx->D, ctx->stream));
-  CU(ctx->kt->fsub(u, ctx->stream));
-  ph_end(ctx, MDN_PHASE_FORWARD, 1);
+  CU(ctx->kt->stage0(u, ctx->stream));
+  if (e0) CU(cudaEventRecord(e0, ctx->stream));
+  if (ctx->D > 1) {
+    CU(ctx->kt->fsub(u, ctx->stream));
+  } else {
+    // residual of the single stage
+    u.first_stage = 1;
+    CU(ctx->kt->fsub(u, ctx->stream));
+  }
+  ph_end(ctx, MDN_PHASE_FORWARD, 3);
   return MDN_OK;
 }
 
-// One Newton step: A_0 and its QR on the side stream while the evaluation
-// runs on the other SMs, then the forward substitution, x += dx and norms.
-static mdn_status run_step(mdn_ctx* ctx, double* x, double* f, double* A, double* dx, double* hist) {
+// Newton steps with the QR of A_0 pipelined across steps.  Step s needs
+// W_s = (A_0 at x^(s))^{-1}; x^(s) has the constant coefficients
+// x_0^(s-1) + dx_0^(s-1), known right after stage 0 of step s-1.  So the A_0
+// and QR of step s run on the side stream (on a third of the SMs) beside the
+// later stages of step s-1, its update and the evaluation of step s (on the
+// other SMs).  A_0 and W alternate between two buffers by step parity.
+static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, bool* converged) {
   const Layout& L = ctx->L;
-  const long long D = ctx->D, n = ctx->n;
+  const long long D = ctx->D, n = ctx->n, nn = n * n, KC = (long long)ctx->K * ctx->C;
+  double* x = ctx->at<double>(L.o_x);
+  double* f = ctx->at<double>(L.o_f);
+  double* dx = ctx->at<double>(L.o_dx);
+  double* A = ctx->at<double>(L.o_A);
+  double* hist = ctx->at<double>(L.o_hist);
+  double* A0b[2] = {ctx->at<double>(L.o_A0b), ctx->at<double>(L.o_A0b) + KC * nn};
+  double* Wb[2] = {ctx->at<double>(L.o_W), ctx->at<double>(L.o_W) + KC * nn};
   const int qb = qr_blocks(ctx);
-  // the QR of A0 runs beside the evaluation when it needs at most a third of
-  // the SMs (the evaluation keeps the rest); otherwise one after the other
   const bool overlap = ctx->side && qb <= ctx->num_sms / 3;
+  const int rest = overlap ? ctx->num_sms - qb : ctx->num_sms;
   mdn_status r;
+  *converged = false;
+  // A_0 and QR of the first step
   if (overlap) {
     CU(cudaEventRecord(ctx->ev_fork, ctx->stream));
     CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-    ph_begin(ctx, MDN_PHASE_QR, ctx->side);
-    if ((r = run_a0(ctx, x, A, ctx->side)) != MDN_OK) return r;
-    if ((r = run_qr(ctx, A, ctx->side)) != MDN_OK) return r;
-    ph_end(ctx, MDN_PHASE_QR, 5, ctx->side);
-    CU(cudaEventRecord(ctx->ev_join, ctx->side));
-    if ((r = run_evaluate(ctx, x, f, A, ctx->num_sms - qb)) != MDN_OK) return r;
-    CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-  } else {
-    if ((r = run_evaluate(ctx, x, f, A, ctx->num_sms)) != MDN_OK) return r;
-    ph_begin(ctx, MDN_PHASE_QR);
-    if ((r = run_a0(ctx, x, A, ctx->stream)) != MDN_OK) return r;
-    if ((r = run_qr(ctx, A, ctx->stream)) != MDN_OK) return r;
-    ph_end(ctx, MDN_PHASE_QR, 5);
   }
-  if ((r = run_forward(ctx, A, f, -1, dx)) != MDN_OK) return r;
-  UpdParams u{};
-  u.n = ctx->n;
-  u.D = ctx->D;
-  u.x = x;
-  u.dx = dx;
-  u.f = f;
-  u.Nx = n * D;
-  u.dxabs = ctx->at<double>(L.o_dxabs);
-  u.fabs = ctx->at<double>(L.o_fabs);
-  u.status = ctx->at<int>(L.o_status);
-  ph_begin(ctx, MDN_PHASE_UPDATE);
-  CU(ctx->kt->update(u, ctx->stream));
-  NormParams np{};
-  np.count = n * D;
-  np.fabs = u.fabs;
-  np.resabs = ctx->at<double>(L.o_resabs);
-  np.dxabs = u.dxabs;
-  np.hist = hist;
-  norms_kernel<<<1, 1024, 0, ctx->stream>>>(np);
-  CU(cudaGetLastError());
-  ph_end(ctx, MDN_PHASE_UPDATE, 2);
+  cudaStream_t qs = overlap ? ctx->side : ctx->stream;
+  ph_begin(ctx, MDN_PHASE_QR, qs);
+  if ((r = run_a0(ctx, x, n * D, ctx->D, A0b[0], nn, qs)) != MDN_OK) return r;
+  if ((r = run_qr(ctx, A0b[0], nn, Wb[0], qs)) != MDN_OK) return r;
+  ph_end(ctx, MDN_PHASE_QR, 5, qs);
+  if (overlap) CU(cudaEventRecord(ctx->ev_join, ctx->side));
+  for (int s = 0; s < steps; ++s) {
+    const int b = s & 1;
+    if ((r = run_evaluate(ctx, x, f, A, rest)) != MDN_OK) return r;
+    if (overlap) CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    const bool next = s + 1 < steps;
+    if ((r = run_forward(ctx, A, A0b[b], nn, Wb[b], f, -1, dx, x, (overlap && next) ? ctx->ev_fork : nullptr,
+                         rest)) != MDN_OK)
+      return r;
+    if (next) {
+      // A_0 and QR of step s+1 from x_0 + dx_0
+      if (overlap) CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+      ph_begin(ctx, MDN_PHASE_QR, qs);
+      if ((r = run_a0(ctx, ctx->at<double>(L.o_xn0), n, 1, A0b[b ^ 1], nn, qs)) != MDN_OK) return r;
+      if ((r = run_qr(ctx, A0b[b ^ 1], nn, Wb[b ^ 1], qs)) != MDN_OK) return r;
+      ph_end(ctx, MDN_PHASE_QR, 5, qs);
+      if (overlap) CU(cudaEventRecord(ctx->ev_join, ctx->side));
+    }
+    UpdParams u{};
+    u.n = ctx->n;
+    u.D = ctx->D;
+    u.x = x;
+    u.dx = dx;
+    u.f = f;
+    u.Nx = n * D;
+    u.dxabs = ctx->at<double>(L.o_dxabs);
+    u.fabs = ctx->at<double>(L.o_fabs);
+    u.status = ctx->at<int>(L.o_status);
+    ph_begin(ctx, MDN_PHASE_UPDATE);
+    CU(ctx->kt->update(u, ctx->stream));
+    NormParams np{};
+    np.count = n * D;
+    np.fabs = u.fabs;
+    np.resabs = ctx->at<double>(L.o_resabs);
+    np.dxabs = u.dxabs;
+    np.hist = hist + 3 * s;
+    norms_kernel<<<1, 1024, 0, ctx->stream>>>(np);
+    CU(cudaGetLastError());
+    ph_end(ctx, MDN_PHASE_UPDATE, 2);
+    *done_out = s + 1;
+    if (tol > 0.0) {
+      double h[3];
+      CU(cudaMemcpyAsync(h, hist + 3 * s, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+      if (h[2] <= tol) {
+        *converged = true;
+        break;
+      }
+    }
+  }
+  // the QR of a step that is not run must be finished before returning
+  if (overlap) CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
   return MDN_OK;
 }
 
@@ -718,28 +777,12 @@ mdn_status mdn_newton(mdn_ctx* ctx, int max_steps, double tol, int* steps_done, 
   if (!ctx->has_series) return fail(ctx, MDN_ESTATE, "no series set");
   if (max_steps < 1 || max_steps > MDN_MAX_STEPS) return fail(ctx, MDN_EINVAL, "max_steps out of range");
   const Layout& L = ctx->L;
-  double* x = ctx->at<double>(L.o_x);
-  double* f = ctx->at<double>(L.o_f);
-  double* dx = ctx->at<double>(L.o_dx);
-  double* A = ctx->at<double>(L.o_A);
   double* hist = ctx->at<double>(L.o_hist);
   CU(cudaMemsetAsync(ctx->at<int>(L.o_status), 0, 4, ctx->stream));
   int done = 0;
   bool converged = false;
-  for (int s = 0; s < max_steps; ++s) {
-    mdn_status r = run_step(ctx, x, f, A, dx, hist + 3 * s);
-    if (r != MDN_OK) return r;
-    done = s + 1;
-    if (tol > 0.0) {
-      double h[3];
-      CU(cudaMemcpyAsync(h, hist + 3 * s, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
-      CU(cudaStreamSynchronize(ctx->stream));
-      if (h[2] <= tol) {
-        converged = true;
-        break;
-      }
-    }
-  }
+  mdn_status r = run_steps(ctx, max_steps, tol, &done, &converged);
+  if (r != MDN_OK) return r;
   if (res_hist) CU(cudaMemcpyAsync(res_hist, hist, sizeof(double) * 3 * done, cudaMemcpyDeviceToHost, ctx->stream));
   mdn_status st = read_status(ctx);
   if (steps_done) *steps_done = done;
@@ -760,7 +803,9 @@ mdn_status mdn_evaluate(mdn_ctx* ctx, const double* x, double* f_out, double* A_
   if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
   if (!x || !f_out) return fail(ctx, MDN_EINVAL, "null pointer argument");
   mdn_status r;
-  if (A_out && (r = run_a0(ctx, x, A_out, ctx->stream)) != MDN_OK) return r;
+  if (A_out && (r = run_a0(ctx, x, (long long)ctx->n * ctx->D, ctx->D, A_out,
+                           (long long)ctx->D * ctx->n * ctx->n, ctx->stream)) != MDN_OK)
+    return r;
   return run_evaluate(ctx, x, f_out, A_out, ctx->num_sms);
 }
 
@@ -769,11 +814,13 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
   if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
   if (!A || !b || !dx) return fail(ctx, MDN_EINVAL, "null pointer argument");
   CU(cudaMemsetAsync(ctx->at<int>(ctx->L.o_status), 0, 4, ctx->stream));
+  const long long DNN = (long long)ctx->D * ctx->n * ctx->n;
+  double* W = ctx->at<double>(ctx->L.o_W);
   ph_begin(ctx, MDN_PHASE_QR);
-  mdn_status r = run_qr(ctx, A, ctx->stream);
+  mdn_status r = run_qr(ctx, A, DNN, W, ctx->stream);
   if (r != MDN_OK) return r;
   ph_end(ctx, MDN_PHASE_QR, 3);
-  if ((r = run_forward(ctx, A, b, +1, dx)) != MDN_OK) return r;
+  if ((r = run_forward(ctx, A, A, DNN, W, b, +1, dx, nullptr, nullptr, ctx->num_sms)) != MDN_OK) return r;
   return read_status(ctx);
 }
 

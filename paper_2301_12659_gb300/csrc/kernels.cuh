@@ -343,7 +343,7 @@ __global__ void a0_partials_kernel(A0Params p) {
   ld(p.coeff, p.Nc, (long long)m * p.D, g);
   for (int q = 0; q < k; ++q) {
     if (q == pos) continue;
-    ld(p.x, p.Nx, (long long)p.vidx[vp + q] * p.D, x);
+    ld(p.x, p.Nx, (long long)p.vidx[vp + q] * p.xstride, x);
     cmd<K, C> r;
     cmd_mul(g, x, r);
     g = r;
@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
     // ---- solve warps: dx_k = W r_k ----
     const int w = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (w >= p.nW) return;
-    for (int k = 0; k < D; ++k) {
+    for (int k = p.first_stage; k < D; ++k) {
       if (!warp_wait(&p.rdone[k], (unsigned)n, p.spin_limit, p.status)) return;
       for (int i = w; i < n; i += p.nW) {
         cmd<K, C> s;
@@ -769,6 +769,7 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
   // initialise: acc = sgn * b_k[i]; stage 0 is final at once
   for (long long q = ow; q < items; q += p.nOwn) {
     const int k = (int)(q / n), i = (int)(q - (long long)k * n);
+    if (k < p.first_stage) continue;  // r_0 stored by stage0_kernel
     cmd<K, C> b;
     ld(p.rhs, p.Nx, (long long)i * D + k, b);
     if (p.rhs_sign < 0) {
@@ -813,12 +814,54 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
       if (k != m) continue;
       // residual of stage m: r_m[i] - (A_0 dx_m)[i]
       cmd<K, C> ax, r, res;
-      warp_rowdot<K, C>(p.A, p.NA, (long long)i * n, p.dx, p.Nx, n, D, m, ax);
+      warp_rowdot<K, C>(p.A0, p.NA0, (long long)i * n, p.dx, p.Nx, n, D, m, ax);
       ld(p.r, p.Nx, (long long)i * D + k, r);
       cmd_sub(r, ax, res);
       if (lane == 0) p.resabs[(long long)i * D + m] = (C == 2) ? hypot(res.re[0], res.im[0]) : fabs(res.re[0]);
     }
   }
+}
+
+// Stage 0 alone, one warp per row: r_0 = sgn b_0, dx_0 = W r_0, and the
+// constant coefficients of the next series, x_0 + dx_0 (the same md addition
+// as the update of x), so that the next step's A_0 and its QR can start early.
+template <int K, int C>
+__global__ void stage0_kernel(FsubParams p) {
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n = p.n, D = p.D;
+  if (i >= n) return;
+  CAcc<K, C> acc;
+  cacc_zero(acc);
+  for (int l = lane; l < n; l += 32) {
+    cmd<K, C> w, b;
+    ld(p.W, p.Nnn, (long long)i * n + l, w);
+    ld(p.rhs, p.Nx, (long long)l * D, b);
+    cacc_fma(acc, w, b);
+  }
+  cmd<K, C> s;
+  warp_sum_acc(acc, s);
+  if (p.rhs_sign < 0) {
+    md_neg(s.re, s.re);
+    md_neg(s.im, s.im);
+  }
+  if (lane == 0) {
+    cmd<K, C> b;
+    ld(p.rhs, p.Nx, (long long)i * D, b);
+    if (p.rhs_sign < 0) {
+      md_neg(b.re, b.re);
+      md_neg(b.im, b.im);
+    }
+    st(p.r, p.Nx, (long long)i * D, b);
+    st(p.dx, p.Nx, (long long)i * D, s);
+    if (p.xnext0) {
+      cmd<K, C> x0, xn;
+      ld(p.x, p.Nx, (long long)i * D, x0);
+      cmd_add(x0, s, xn);
+      st(p.xnext0, n, i, xn);
+    }
+  }
+  warp_count(&p.xdone[0]);
 }
 
 // x += dx; per-entry magnitudes of f and dx for the norms of the step.
@@ -919,6 +962,11 @@ cudaError_t launch_fsub(const FsubParams& p, cudaStream_t s) {
                                      QR_SMEM_RESERVE, s);
 }
 template <int K, int C>
+cudaError_t launch_stage0(const FsubParams& p, cudaStream_t s) {
+  stage0_kernel<K, C><<<(p.n + 3) / 4, 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+template <int K, int C>
 cudaError_t launch_update(const UpdParams& p, cudaStream_t s) {
   update_kernel<K, C><<<grid_for((long long)p.n * p.D, 128), 128, 0, s>>>(p);
   return cudaGetLastError();
@@ -927,7 +975,7 @@ cudaError_t launch_update(const UpdParams& p, cudaStream_t s) {
 template <int K, int C>
 const KernelTable* make_table() {
   static const KernelTable t = {K, C, &launch_ed<K, C>, &launch_a0<K, C>, &ed_blocks_per_sm<K, C>, &launch_assemble<K, C>,
-                                &launch_qr<K, C>, &launch_fsub<K, C>,
+                                &launch_qr<K, C>, &launch_fsub<K, C>, &launch_stage0<K, C>,
                                 &launch_update<K, C>};
   return &t;
 }

@@ -48,6 +48,7 @@ struct A0Params {
   int n, D, M;
   const double* x;
   long long Nx;
+  int xstride;  // distance between the constant coefficients of two variables in x
   const double* coeff;
   long long Nc;
   const int* mono_k;
@@ -103,14 +104,19 @@ struct QrParams {
 // Persistent forward substitution (one cooperative launch per solve).
 struct FsubParams {
   int n, D, rhs_sign;
+  int first_stage;  // 1 when stage 0 (dx_0 = W r_0) was done by stage0_kernel
   int nW;       // solve warps (dx_k = W r_k), on the first nW/4 blocks
   int nOwn;     // owner warps of the r_k[i] accumulators
   const double* A;
-  long long NA;  // D*n*n
+  long long NA;  // D*n*n (slices j >= 1 are read)
+  const double* A0;
+  long long NA0;  // stride of the array holding A_0
   const double* W;
   long long Nnn;
   const double* rhs;
   double* r;     // accumulators, then r_k[i]   [K][C][n][D]
+  const double* x;   // stage0_kernel: current series, x_0 + dx_0 goes to xnext0
+  double* xnext0;    // [K][C][n]
   double* dx;
   long long Nx;  // n*D
   double* resabs;
@@ -148,6 +154,7 @@ struct KernelTable {
   cudaError_t (*assemble)(const AsmParams&, bool want_A, cudaStream_t);
   cudaError_t (*qr)(const QrParams&, cudaStream_t);  // QR, Q^H, R^{-1}, then W = R^{-1} Q^H
   cudaError_t (*fsub)(const FsubParams&, cudaStream_t);
+  cudaError_t (*stage0)(const FsubParams&, cudaStream_t);
   cudaError_t (*update)(const UpdParams&, cudaStream_t);
 };
 

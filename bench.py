@@ -66,6 +66,25 @@ def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def aggregate_over_ranks(total_ms: float, steps: int, device=None):
+    """Replicas: every rank ran `steps` Newton steps of its own copy of the
+    workload (no collective on the data path).  Returns (max time over ranks
+    in ms, whole-job steps/s = world * steps / max time)."""
+    world = 1
+    t_max = float(total_ms)
+    try:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            import torch
+            world = dist.get_world_size()
+            t = torch.tensor([t_max], dtype=torch.float64, device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_max = float(t.item())
+    except ImportError:
+        pass
+    return t_max, world * steps / (t_max * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -236,14 +255,9 @@ def run_ours(args, cfg):
     _, phase_ms, launches = md.mdn_profile(nw.ctx, 0)
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t_max = total_ms
+    t_max, value = aggregate_over_ranks(total_ms, args.steps, device=dev)
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        dist.barrier()
-    value = world * args.steps / (t_max * 1e-3)
+        torch.distributed.barrier()
 
     # end to end: whole solves from pinned host memory through the API
     x0_host = torch.from_numpy(x0).pin_memory()

@@ -387,40 +387,46 @@ __global__ void a0_assemble_kernel(A0Params p) {
 //   col[j]  x_j is published (rows j..n-1 of Vm column j);
 //   ref[j]  the scalars s_j|x_j|, v_jj and tau_j are published;
 //   rinv[j] 1 / R_jj is published.
-// Look-ahead: the warp of column c forms x_j^H y_c (and, for j = c-1, |y_c|^2
-// over rows c-1..n-1) as soon as col[j] appears, while the owner of column j
-// is still computing its scalars; when ref[j] appears, applying H_j costs
-//   w = x_j^H y_c + conj(s_j|x_j|) y_c[j],   y_c -= tau_j w v_j,
-// and the norm of the next column follows by downdating,
-//   |y_c'[c..]|^2 = |y_c[c-1..]|^2 - |y_c'[c-1]|^2  (H_{c-1} is unitary),
-// recomputed directly if that loses more than 8 bits.
+// Look-ahead: the warp of column c forms x_j^H y_c as soon as col[j]
+// appears, while the owner of column j is still computing its scalars; when
+// ref[j] appears, applying H_j costs
+//   w = x_j^H y_c + conj(s_j|x_j|) y_c[j],   y_c -= tau_j w v_j.
+// The norm of the pivot column needs no reduction on the chain: the
+// reflectors are unitary, so rows j+1..n-1 of y_c after H_j hold
+// |a_c|^2 - sum_{i<=j} |R_ic|^2 (a_c = column c of A0), accumulated as each
+// R_ic becomes final and recomputed directly if more than 8 bits cancel.
 
-// acc += conj(x_j[i]) y[i] over rows i = j..n-1 (x_j from Vm), and, if
-// with_norm, nrm += |y[i]|^2 over the same rows.
+// dot = sum of conj(x_j[i]) y[i] over rows i = j..n-1 (x_j from Vm).
 template <int K, int C>
-__device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const double* y, bool with_norm,
-                                             cmd<K, C>& dot, double (&nrm)[K]) {
+__device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const double* y, cmd<K, C>& dot) {
   const int lane = threadIdx.x & 31;
   const int n = p.n;
-  CAcc<K, C> acc, an;
+  CAcc<K, C> acc;
   cacc_zero(acc);
-  cacc_zero(an);
   for (int i = j + lane; i < n; i += 32) {
     cmd<K, C> x, yi;
     ld(p.Vm, p.Nnn, (long long)i * n + j, x);
     ld(y, n, i, yi);
     cacc_fma_conj(acc, x, yi);
-    if (with_norm) {
-      acc_fma(an.re, yi.re, yi.re);
-      if constexpr (C == 2) acc_fma(an.re, yi.im, yi.im);
-    }
   }
   warp_sum_acc(acc, dot);
-  if (with_norm) {
-    cmd<K, C> t;
-    warp_sum_acc(an, t);
-    md_copy(t.re, nrm);
+}
+
+// |y|^2 over rows i0..n-1, every lane gets it.
+template <int K, int C>
+__device__ __forceinline__ void qr_norm2(const double* y, int n, int i0, double (&nrm)[K]) {
+  const int lane = threadIdx.x & 31;
+  CAcc<K, C> ca;
+  cacc_zero(ca);
+  for (int i = i0 + lane; i < n; i += 32) {
+    cmd<K, C> v;
+    ld(y, n, i, v);
+    acc_fma(ca.re, v.re, v.re);
+    if constexpr (C == 2) acc_fma(ca.re, v.im, v.im);
   }
+  cmd<K, C> t;
+  warp_sum_acc(ca, t);
+  md_copy(t.re, nrm);
 }
 
 // y -= tau_j w v_j with w = dot + conj(salpha_j) y[j] (rows j..n-1).
@@ -470,18 +476,25 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
     st(y, n, i, v);
   }
   __syncwarp();
-  double pre_norm[K];
-  md_zero(pre_norm);
+  // |a_c|^2, then minus |R_jc|^2 as each R_jc is final
+  double norm0[K];
+  qr_norm2<K, C>(y, n, 0, norm0);
+  Acc<K> nacc;
+  acc_set(nacc, norm0);
   for (int j = 0; j < c; ++j) {
     if (!warp_wait(&fcol[j], ep, p.spin_limit, p.status)) return;
     cmd<K, C> dot;
-    qr_lookahead<K, C>(p, j, y, j == c - 1, dot, pre_norm);
+    qr_lookahead<K, C>(p, j, y, dot);
     if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
     qr_apply_la<K, C>(p, j, y, dot);
-    if (lane == 0) {
-      cmd<K, C> v;
-      ld(y, n, j, v);
-      st(p.Rm, p.Nnn, (long long)j * n + c, v);  // R[j][c] is final
+    cmd<K, C> v, nv;
+    ld(y, n, j, v);
+    if (lane == 0) st(p.Rm, p.Nnn, (long long)j * n + c, v);  // R[j][c] is final
+    md_neg(v.re, nv.re);
+    acc_fma(nacc, nv.re, v.re);
+    if constexpr (C == 2) {
+      md_neg(v.im, nv.im);
+      acc_fma(nacc, nv.im, v.im);
     }
   }
   // publish x_c (rows c..n-1)
@@ -491,32 +504,14 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
     st(p.Vm, p.Nnn, (long long)i * n + c, v);
   }
   warp_publish(&fcol[c], ep);
-  // N = |x_c|^2 by downdating (direct for c = 0 or on cancellation)
+  // N = |x_c|^2 by downdating (recomputed on cancellation)
   double N[K];
-  bool direct = (c == 0);
-  if (!direct) {
-    double t[K];
-    cmd<K, C> yp;
-    ld(y, n, c - 1, yp);
-    cmd_abs2(yp, t);
-    md_sub(pre_norm, t, N);
+  acc_get(nacc, N);
+  if (c > 0) {
     // more than 8 bits lost (or a negative difference): recompute
     const unsigned long long eN = (unsigned long long)__double_as_longlong(N[0]) >> 52;
-    const unsigned long long eP = (unsigned long long)__double_as_longlong(pre_norm[0]) >> 52;
-    direct = (__double_as_longlong(N[0]) <= 0) || (eN + 8 < eP);
-  }
-  if (direct) {
-    CAcc<K, C> ca;
-    cacc_zero(ca);
-    for (int i = c + lane; i < n; i += 32) {
-      cmd<K, C> v;
-      ld(y, n, i, v);
-      acc_fma(ca.re, v.re, v.re);
-      if constexpr (C == 2) acc_fma(ca.re, v.im, v.im);
-    }
-    cmd<K, C> t;
-    warp_sum_acc(ca, t);
-    md_copy(t.re, N);
+    const unsigned long long eP = (unsigned long long)__double_as_longlong(norm0[0]) >> 52;
+    if ((__double_as_longlong(N[0]) <= 0) || (eN + 8 < eP)) qr_norm2<K, C>(y, n, c, N);
   }
   const bool singular = !nonzero(N[0]);
   if (singular) N[0] = 1.0;  // keep the arithmetic finite; reported below
@@ -549,7 +544,15 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
     }
   }
   cmd<K, C> salpha, v0;
-  cmd_scale(sg, alpha, salpha);
+  if constexpr (C == 1) {
+    // s = +-1: s |x_c| is a sign change
+    const bool neg = sg.re[0] < 0.0;
+#pragma unroll
+    for (int l = 0; l < K; ++l) salpha.re[l] = neg ? -alpha[l] : alpha[l];
+    md_zero(salpha.im);
+  } else {
+    cmd_scale(sg, alpha, salpha);
+  }
   cmd_add(x0, salpha, v0);
   double t1[K], t2[K], tau[K];
   md_mul(alpha, ax0, t1);
@@ -597,8 +600,7 @@ __device__ void qr_identity(const QrParams& p, int e, double* y, unsigned ep) {
   for (int j = 0; j < n; ++j) {
     if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
     cmd<K, C> dot;
-    double dummy[K];
-    qr_lookahead<K, C>(p, j, y, false, dot, dummy);
+    qr_lookahead<K, C>(p, j, y, dot);
     qr_apply_la<K, C>(p, j, y, dot);
   }
   for (int i = lane; i < n; i += 32) {

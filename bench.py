@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--e2e-solves", type=int, default=5)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--late-updates", type=int, default=0, metavar="FIRST_STAGE",
+                    help="stated-accuracy variant: stages k >= FIRST_STAGE form their updates in K/2 limbs")
     return ap.parse_args()
 
 
@@ -181,7 +183,8 @@ def dtype_name(cfg):
 
 
 def config_dict(cfg, args):
-    return {"workload": cfg.name, "limbs": cfg.K, "complex": cfg.C == 2, "n": cfg.n, "degree": cfg.d,
+    late = {"late_updates": {"first_stage": args.late_updates, "limbs": cfg.K // 2}} if args.late_updates else {}
+    return {**late, "workload": cfg.name, "limbs": cfg.K, "complex": cfg.C == 2, "n": cfg.n, "degree": cfg.d,
             "monomials_per_equation": cfg.mono_per_eq, "vars_per_monomial": [cfg.kmin, cfg.kmax],
             "newton_steps_per_solve": cfg.steps, "parallelism": f"replicas x{args.gpus}",
             "l2": "flushed between timed solves (256 MiB write); steps run in solves of "
@@ -204,6 +207,8 @@ def run_ours(args, cfg):
     s, xstar, x0 = wl.planted_system(cfg)
     s.cst = None
     nw = md.Newton(s)
+    if args.late_updates:
+        nw.set_late_updates(args.late_updates, cfg.K // 2)
     # constant term planting x*: minus the system at x* (evaluated here)
     cst = -nw.evaluate(xstar, want_A=False)
     nw.set_constant(cst)

@@ -136,6 +136,17 @@ mdn_status mdn_evaluate(mdn_ctx* ctx, const double* x, double* f_out, double* A_
  * MDN_ESINGULAR for a zero pivot. */
 mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx);
 
+/* Stated-accuracy variant of the forward substitution (the multiple double
+ * arithmetic of Section 1 with the mixed-precision remark there, applied to
+ * the right hand side updates of Section 5.4): stages k >= first_stage form
+ * their block updates sum_{j>=1} A_j dx_{k-j} in `limbs` limbs, reading the
+ * leading `limbs` doubles of every K-limb operand; the stage's right hand side
+ * b_k, the solve dx_k = A0^{-1} r_k, the QR of A0, the residuals and the
+ * evaluation stay in K limbs.  limbs must be K (variant off) or K/2 (K >= 2);
+ * 1 <= first_stage, and first_stage > d switches the variant off.  Applies to
+ * later mdn_newton and mdn_solve calls on the context.  Default: off. */
+mdn_status mdn_set_late_updates(mdn_ctx* ctx, int first_stage, int limbs);
+
 /* Phases of a Newton step for mdn_profile(), after the kernel types of the
  * paper's Table 3 (Section 6.2): evaluation and differentiation
  * ("convolutions"), assembly of f and A, Householder QR with Q^H and back
@@ -155,6 +166,58 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
  * accumulated milliseconds (ms_out) and kernel launch counts (launches_out)
  * per phase into host arrays of MDN_NUM_PHASES entries (either may be NULL). */
 mdn_status mdn_profile(mdn_ctx* ctx, int enable, double* ms_out, int64_t* launches_out);
+
+/* ---------------------------------------------------------------------------
+ * Batched systems: many independent systems (each its own n, degree and
+ * monomials, one K and C for all) solved in one persistent launch, each run
+ * to its stop rule.  The paper's method (Section 2, with the kernels of
+ * Sections 5.1-5.4) applied to every system; the batching itself, the work
+ * queue and the stop rule are this library's.
+ *
+ * Packed layout.  System s has n_s equations and unknowns, D_s = degree_s+1
+ * coefficients and M_s monomials; its monomials are the global indices
+ * mono_s .. mono_s + M_s - 1 with mono_s = sum_{t<s} M_t.  Host arrays:
+ * eq_of_monomial [Mtot] (equation within the system), var_ptr [Mtot+1] (CSR
+ * offsets into var_idx, var_ptr[0] = 0), var_idx (variable within the
+ * system; a repeat is a power).  Device arrays: coeff is the concatenation
+ * over s of [K][C][M_s][D_s] blocks; const_term, x and f are concatenations
+ * of [K][C][n_s][D_s] blocks, block s starting at sum_{t<s} K*C*n_t*D_t.
+ *
+ * Stop rule of mdn_batch_solve: ||f(x)||_inf <= tol before an update, or
+ * ||dx||_inf <= tol * max(1, ||x||_inf) after one (leading doubles), or
+ * max_steps updates.  steps_out[s] counts the updates applied; flags_out[s]
+ * has bit 0 set when the stop rule was met, bit 1 for a zero pivot in the QR
+ * of A_0 (system left at its last x), bit 2 for a non-finite value.
+ *
+ * Tiles: threads_per_block (multiple of 32, 128..1024, at least the largest
+ * n) and blocks_per_sm (at most what the kernel's registers allow); 0 picks
+ * 256 threads and the largest resident count.  Sizes: 1 <= n_s <= 128,
+ * 0 <= degree_s <= 63, every monomial of at most 16 variables. */
+typedef struct mdn_batch mdn_batch;
+
+mdn_status mdn_batch_create(mdn_batch** out, int limbs, int is_complex, int count, const int32_t* n,
+                            const int32_t* degree, const int32_t* n_monomials, int threads_per_block,
+                            int blocks_per_sm);
+/* Workspace for the system structure var_ptr (host [Mtot+1]); 0 on error. */
+size_t mdn_batch_workspace_bytes(const mdn_batch* b, const int32_t* var_ptr);
+/* Builds the tables on the host and copies them into the workspace (a device
+ * buffer of ws_bytes >= mdn_batch_workspace_bytes, 256-byte aligned, borrowed
+ * until mdn_batch_destroy).  coeff and const_term are borrowed device arrays.
+ * Work is enqueued on `cuda_stream`. */
+mdn_status mdn_batch_load(mdn_batch* b, const int32_t* eq_of_monomial, const int32_t* var_ptr,
+                          const int32_t* var_idx, const double* coeff, const double* const_term, void* workspace,
+                          size_t ws_bytes, void* cuda_stream);
+/* f(x) of every system (device, packed); synchronises. */
+mdn_status mdn_batch_evaluate(mdn_batch* b, const double* x, double* f_out);
+/* Newton on every system from x0 (device, packed) into x (device, packed,
+ * may equal x0), one persistent launch replayed from a CUDA graph; the host
+ * arrays steps_out and flags_out [count] are filled; synchronises. */
+mdn_status mdn_batch_solve(mdn_batch* b, const double* x0, double* x, int max_steps, double tol, int32_t* steps_out,
+                           int32_t* flags_out);
+/* The tiles in use. */
+mdn_status mdn_batch_tiles(const mdn_batch* b, int* threads_per_block, int* blocks_per_sm);
+const char* mdn_batch_last_error(const mdn_batch* b);
+void mdn_batch_destroy(mdn_batch* b);
 
 /* Size of the static device scratch of mdn_evaluate_static(). */
 #define MDN_STATIC_SCRATCH_BYTES (2u << 20)

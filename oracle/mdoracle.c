@@ -612,7 +612,22 @@ static int back_sub(const qr_t *Q, const mdc *y, mdc *x) {
 /* ------------------------------------------------------------------------- */
 
 /* A [(d+1)][n][n], B and DX [n][d+1]: sum_{j<=k} A_j DX_{k-j} = B_k. */
-static int block_solve(int K, int C, int n, int d, const mdc *A, const mdc *B, mdc *DX) {
+/* x rounded to L <= K limbs. */
+static void mdc_round_to(const mdc *x, int K, int C, int L, mdc *out) {
+    cacc_t *t = (cacc_t *)malloc(sizeof(cacc_t));
+    cacc_init(t);
+    cacc_add(t, x, K, C, 1.0);
+    cacc_round(t, L, C, out);
+    free(t);
+}
+
+/* Forward substitution of Section 5.4.  Stages k >= late_stage (the
+ * stated-accuracy variant) form their update sum_{j>=1} A_j dx_{k-j} in
+ * late_K limbs: every operand rounded to late_K limbs, the sum rounded to
+ * late_K limbs, then subtracted from b_k in K limbs.  late_stage > d: the
+ * plain method. */
+static int block_solve(int K, int C, int n, int d, const mdc *A, const mdc *B, mdc *DX, int late_stage,
+                       int late_K) {
     const int D = d + 1;
     qr_t Q;
     int rc = qr_factor(A, n, K, C, &Q);
@@ -628,9 +643,26 @@ static int block_solve(int K, int C, int n, int d, const mdc *A, const mdc *B, m
             cacc_t *t = (cacc_t *)malloc(sizeof(cacc_t));
             cacc_init(t);
             cacc_add(t, &B[(size_t)i * D + k], K, C, 1.0);
-            for (int j = 1; j <= k; ++j)
-                for (int l = 0; l < n; ++l)
-                    cacc_add_prod(t, &A[((size_t)j * n + i) * n + l], &DX[(size_t)l * D + (k - j)], K, C, -1.0);
+            if (k >= late_stage && late_K < K) {
+                cacc_t *u = (cacc_t *)malloc(sizeof(cacc_t));
+                cacc_init(u);
+                for (int j = 1; j <= k; ++j)
+                    for (int l = 0; l < n; ++l) {
+                        mdc a, x;
+                        mdc_round_to(&A[((size_t)j * n + i) * n + l], K, C, late_K, &a);
+                        mdc_round_to(&DX[(size_t)l * D + (k - j)], K, C, late_K, &x);
+                        cacc_add_prod(u, &a, &x, late_K, C, 1.0);
+                    }
+                mdc upd;
+                cacc_round(u, late_K, C, &upd);
+                cacc_add(t, &upd, late_K, C, -1.0);
+                free(u);
+            } else {
+                for (int j = 1; j <= k; ++j)
+                    for (int l = 0; l < n; ++l)
+                        cacc_add_prod(t, &A[((size_t)j * n + i) * n + l], &DX[(size_t)l * D + (k - j)], K, C,
+                                      -1.0);
+            }
             cacc_round(t, K, C, &r[i]);
             free(t);
         }
@@ -828,14 +860,19 @@ int orc_qr(int K, int C, int n, const double *A0, double *Qout, double *Rout) {
 }
 
 int orc_solve(int K, int C, int n, int d, const double *A, const double *b, double *dx) {
-    if (check_kc(K, C) || n < 1 || d < 0) return ORC_EINVAL;
+    return orc_solve_late(K, C, n, d, A, b, d + 1, K, dx);
+}
+
+int orc_solve_late(int K, int C, int n, int d, const double *A, const double *b, int late_stage, int late_K,
+                   double *dx) {
+    if (check_kc(K, C) || n < 1 || d < 0 || late_K < 1 || late_K > K) return ORC_EINVAL;
     const long D = d + 1;
     mdc *AA = (mdc *)malloc(sizeof(mdc) * (size_t)D * n * n);
     mdc *B = (mdc *)malloc(sizeof(mdc) * (size_t)n * D);
     mdc *X = (mdc *)calloc((size_t)n * D, sizeof(mdc));
     soa_to_mdc(A, K, C, D * n * n, AA);
     soa_to_mdc(b, K, C, (long)n * D, B);
-    int rc = block_solve(K, C, n, d, AA, B, X);
+    int rc = block_solve(K, C, n, d, AA, B, X, late_stage, late_K);
     mdc_to_soa(X, K, C, (long)n * D, dx);
     free(X);
     free(B);
@@ -846,7 +883,14 @@ int orc_solve(int K, int C, int n, int d, const double *A, const double *b, doub
 int orc_newton(int K, int C, int n, int d, int M, const int32_t *eq, const int32_t *vptr,
                const int32_t *vidx, const double *coeff, const double *cst, const double *x0,
                int steps, double *x_out, double *hist) {
-    if (check_kc(K, C) || check_structure(n, d, M, eq, vptr, vidx) || steps < 0) return ORC_EINVAL;
+    return orc_newton_late(K, C, n, d, M, eq, vptr, vidx, coeff, cst, x0, steps, d + 1, K, x_out, hist);
+}
+
+int orc_newton_late(int K, int C, int n, int d, int M, const int32_t *eq, const int32_t *vptr,
+                    const int32_t *vidx, const double *coeff, const double *cst, const double *x0,
+                    int steps, int late_stage, int late_K, double *x_out, double *hist) {
+    if (check_kc(K, C) || check_structure(n, d, M, eq, vptr, vidx) || steps < 0 || late_K < 1 || late_K > K)
+        return ORC_EINVAL;
     const long D = d + 1, N = (long)n * D;
     mdc *CF = (mdc *)malloc(sizeof(mdc) * (size_t)(M > 0 ? M : 1) * D);
     mdc *CS = (mdc *)malloc(sizeof(mdc) * (size_t)N);
@@ -870,7 +914,7 @@ int orc_newton(int K, int C, int n, int d, int M, const int32_t *eq, const int32
                 B[i].im[l] = -F[i].im[l];
             }
         for (long i = 0; i < N; ++i) mdc_zero(&DX[i]);
-        rc = block_solve(K, C, n, d, AA, B, DX);
+        rc = block_solve(K, C, n, d, AA, B, DX, late_stage, late_K);
         if (rc != ORC_OK) break;
         hist[3 * s + 1] = toeplitz_residual(K, C, n, d, AA, B, DX);
         cacc_t *t = (cacc_t *)malloc(sizeof(cacc_t));

@@ -66,6 +66,11 @@ int orc_qr(int K, int C, int n, const double *A0, double *Q, double *R);
  * by Householder QR of A0 and forward substitution.  A [K][C][d+1][n][n],
  * b and dx [K][C][n][d+1]. */
 int orc_solve(int K, int C, int n, int d, const double *A, const double *b, double *dx);
+/* The same with the stated-accuracy variant of the updates: stages
+ * k >= late_stage form sum_{j>=1} A_j dx_{k-j} in late_K limbs (operands and
+ * sum rounded to late_K limbs), everything else in K limbs. */
+int orc_solve_late(int K, int C, int n, int d, const double *A, const double *b, int late_stage, int late_K,
+                   double *dx);
 
 /* Newton's method on power series (Section 2 pseudo code): `steps` iterations
  * from x0, no early exit.  x_out [K][C][n][d+1]; hist [steps][3] holds per
@@ -74,6 +79,10 @@ int orc_solve(int K, int C, int n, int d, const double *A, const double *b, doub
 int orc_newton(int K, int C, int n, int d, int M, const int32_t *eq, const int32_t *vptr,
                const int32_t *vidx, const double *coeff, const double *cst, const double *x0,
                int steps, double *x_out, double *hist);
+/* Newton with the late-update variant of orc_solve_late in every step. */
+int orc_newton_late(int K, int C, int n, int d, int M, const int32_t *eq, const int32_t *vptr,
+                    const int32_t *vidx, const double *coeff, const double *cst, const double *x0,
+                    int steps, int late_stage, int late_K, double *x_out, double *hist);
 
 #ifdef __cplusplus
 }

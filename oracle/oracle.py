@@ -66,8 +66,11 @@ def lib():
             L.orc_qr.argtypes = [i, i, i, P, P, P]
             L.orc_solve.argtypes = [i, i, i, i, P, P, P]
             L.orc_newton.argtypes = [i, i, i, i, i, P, P, P, P, P, P, i, P, P]
+            L.orc_solve_late.argtypes = [i, i, i, i, P, P, i, i, P]
+            L.orc_newton_late.argtypes = [i, i, i, i, i, P, P, P, P, P, P, i, i, i, P, P]
             for name in ("orc_md_binary", "orc_md_sqrt", "orc_series_mul", "orc_evaluate",
-                         "orc_planted_constant", "orc_qr", "orc_solve", "orc_newton"):
+                         "orc_planted_constant", "orc_qr", "orc_solve", "orc_newton", "orc_solve_late",
+                         "orc_newton_late"):
                 getattr(L, name).restype = i
             _lib = L
     return _lib
@@ -166,22 +169,29 @@ def qr(A0):
     return Q, R
 
 
-def solve(A, b) -> np.ndarray:
-    """Block lower triangular Toeplitz solve: A [K,C,d+1,n,n], b [K,C,n,d+1]."""
+def solve(A, b, late=None) -> np.ndarray:
+    """Block lower triangular Toeplitz solve: A [K,C,d+1,n,n], b [K,C,n,d+1].
+    late = (first_stage, limbs): the stated-accuracy variant whose stages
+    k >= first_stage form their updates in `limbs` limbs."""
     A, b = _f64(A), _f64(b)
     K, C, D, n, _ = A.shape
     dx = np.zeros_like(b)
-    _check(lib().orc_solve(K, C, n, D - 1, _p(A), _p(b), _p(dx)), "solve")
+    if late is None:
+        _check(lib().orc_solve(K, C, n, D - 1, _p(A), _p(b), _p(dx)), "solve")
+    else:
+        _check(lib().orc_solve_late(K, C, n, D - 1, _p(A), _p(b), int(late[0]), int(late[1]), _p(dx)), "solve")
     return dx
 
 
-def newton(sysm, x0, steps: int):
-    """`steps` Newton iterations from x0; returns (x, hist[steps, 3])."""
+def newton(sysm, x0, steps: int, late=None):
+    """`steps` Newton iterations from x0; returns (x, hist[steps, 3]).
+    late = (first_stage, limbs) as in solve()."""
     K, C, n, d, M, eq, vptr, vidx, coeff = _sysargs(sysm)
     cst = _f64(sysm.cst)
     x0 = _f64(x0)
     x = np.zeros_like(x0)
     hist = np.zeros((max(steps, 1), 3))
-    _check(lib().orc_newton(K, C, n, d, M, _p(eq), _p(vptr), _p(vidx), _p(coeff), _p(cst), _p(x0),
-                            int(steps), _p(x), _p(hist)), "newton")
+    ls, lk = (d + 1, K) if late is None else (int(late[0]), int(late[1]))
+    _check(lib().orc_newton_late(K, C, n, d, M, _p(eq), _p(vptr), _p(vidx), _p(coeff), _p(cst), _p(x0),
+                                 int(steps), ls, lk, _p(x), _p(hist)), "newton")
     return x, hist[:steps]

@@ -181,6 +181,7 @@ struct mdn_ctx {
       pair_slot, occ;
   std::vector<int4> sched;
   bool loaded = false, has_series = false;
+  int late_stage = 1 << 30;  // stages from here form their updates in K/2 limbs
   const double* coeff = nullptr;
   const double* cst = nullptr;
   cudaStream_t stream = nullptr;
@@ -643,6 +644,7 @@ static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, l
   u.nW = std::min(ctx->n, 4 * FSUB_WBLOCKS);
   const int wb = (u.nW + 3) / 4;
   u.nOwn = (int)std::min<long long>(4LL * std::max(1, blocks - wb), (long long)ctx->n * ctx->D);
+  u.late_stage = std::min(ctx->late_stage, ctx->D);
   u.A = A;
   u.NA = D * n * n;
   u.A0 = A0;
@@ -822,6 +824,18 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
   ph_end(ctx, MDN_PHASE_QR, 3);
   if ((r = run_forward(ctx, A, A, DNN, W, b, +1, dx, nullptr, nullptr, ctx->num_sms)) != MDN_OK) return r;
   return read_status(ctx);
+}
+
+mdn_status mdn_set_late_updates(mdn_ctx* ctx, int first_stage, int limbs) {
+  if (!ctx) return MDN_EINVAL;
+  if (first_stage < 1) return fail(ctx, MDN_EINVAL, "first_stage must be >= 1");
+  if (limbs == ctx->K) {
+    ctx->late_stage = 1 << 30;
+    return MDN_OK;
+  }
+  if (ctx->K < 2 || limbs != ctx->K / 2) return fail(ctx, MDN_EINVAL, "limbs must be K or K/2");
+  ctx->late_stage = first_stage;
+  return MDN_OK;
 }
 
 mdn_status mdn_status_word(mdn_ctx* ctx) {

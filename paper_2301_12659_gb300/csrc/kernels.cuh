@@ -796,7 +796,24 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
       if (k <= m) continue;
       // r_k[i] -= (A_{k-m} dx_m)[i]
       cmd<K, C> ax;
-      warp_rowdot<K, C>(p.A, p.NA, (long long)(k - m) * nn + (long long)i * n, p.dx, p.Nx, n, D, m, ax);
+      if constexpr (K >= 2) {
+        if (k >= p.late_stage) {
+          // the leading K/2 doubles of A and dx are K/2-limb values (limb
+          // index outermost in the layout): the same pointers and strides
+          cmd<K / 2, C> h;
+          warp_rowdot<K / 2, C>(p.A, p.NA, (long long)(k - m) * nn + (long long)i * n, p.dx, p.Nx, n, D, m, h);
+          cmd_zero(ax);
+#pragma unroll
+          for (int l = 0; l < K / 2; ++l) {
+            ax.re[l] = h.re[l];
+            ax.im[l] = h.im[l];
+          }
+        } else {
+          warp_rowdot<K, C>(p.A, p.NA, (long long)(k - m) * nn + (long long)i * n, p.dx, p.Nx, n, D, m, ax);
+        }
+      } else {
+        warp_rowdot<K, C>(p.A, p.NA, (long long)(k - m) * nn + (long long)i * n, p.dx, p.Nx, n, D, m, ax);
+      }
       CAcc<K, C> a;
       ld_acc(p.r, p.Nx, (long long)i * D + k, a);
       cacc_add(a, ax, -1.0);
@@ -972,14 +989,6 @@ template <int K, int C>
 cudaError_t launch_update(const UpdParams& p, cudaStream_t s) {
   update_kernel<K, C><<<grid_for((long long)p.n * p.D, 128), 128, 0, s>>>(p);
   return cudaGetLastError();
-}
-
-template <int K, int C>
-const KernelTable* make_table() {
-  static const KernelTable t = {K, C, &launch_ed<K, C>, &launch_a0<K, C>, &ed_blocks_per_sm<K, C>, &launch_assemble<K, C>,
-                                &launch_qr<K, C>, &launch_fsub<K, C>, &launch_stage0<K, C>,
-                                &launch_update<K, C>};
-  return &t;
 }
 
 }  // namespace mdn

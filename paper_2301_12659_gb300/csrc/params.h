@@ -107,6 +107,7 @@ struct FsubParams {
   int first_stage;  // 1 when stage 0 (dx_0 = W r_0) was done by stage0_kernel
   int nW;       // solve warps (dx_k = W r_k), on the first nW/4 blocks
   int nOwn;     // owner warps of the r_k[i] accumulators
+  int late_stage;  // stages k >= late_stage form their updates in K/2 limbs (D: never)
   const double* A;
   long long NA;  // D*n*n (slices j >= 1 are read)
   const double* A0;
@@ -146,6 +147,54 @@ struct NormParams {
 };
 
 // Launchers of one (K, C) instantiation.
+// ---- batched systems (one persistent launch) ----
+struct BatchSys {
+  int n, D, M, mono0;      // monomials mono0 .. mono0+M-1 (global numbering)
+  int eq0;                 // eq_ptr[eq0 .. eq0+n] delimit the monomials of each equation
+  int pad;
+  long long coeff_off;     // doubles: start of this system's [K][C][M][D] coefficients
+  long long series_off;    // doubles: start of its [K][C][n][D] series (x, constant term, f)
+};
+
+enum : int { BATCH_CONVERGED = 1, BATCH_SINGULAR = 2, BATCH_NONFINITE = 4 };
+
+struct BatchParams {
+  int count, max_steps, evaluate_only, S3;  // S3: scratch series per lane group
+  double tol;
+  const BatchSys* sys;
+  const int* order;    // systems in decreasing estimated cost
+  const int* eq_ptr;   // per system n+1 offsets into eq_mon
+  const int* eq_mon;   // monomials grouped by equation, larger ones first
+  const int* vptr;     // [Mtot+1] CSR offsets (global)
+  const int* vidx;     // variable of each occurrence (local to its system)
+  const double* coeff;
+  const double* cst;
+  double* x;           // packed series, updated in place
+  double* f_out;       // evaluate_only: packed f(x)
+  double* work;        // per-block scratch
+  long long work_stride;  // doubles per block
+  int* queue;
+  int* steps_out;
+  int* flags_out;
+};
+
+__host__ __device__ inline long long batch_work_doubles(int K, int C, int n, int D, int threads, int S3) {
+  const int W = threads / 32, P = (D + 1) / 2, G = 32 / P;
+  const long long KC = (long long)K * C;
+  const long long nn = (long long)n * n;
+  long long s = 0;
+  s += KC * D * nn;                      // A
+  s += 2 * KC * n * D;                   // f, dx
+  s += KC * nn;                          // Y, then W
+  s += KC * n;                           // r
+  s += (long long)K * n;                 // tau
+  s += 3 * KC * n;                       // s|x|, v0, 1/R_jj
+  s += KC * threads;                     // partial sums
+  s += KC * (long long)W * G * S3 * D;   // products of the evaluation
+  return s + 64;
+}
+
+
 struct KernelTable {
   int K, C;
   cudaError_t (*ed)(const EdParams&, int grid, cudaStream_t);
@@ -156,6 +205,8 @@ struct KernelTable {
   cudaError_t (*fsub)(const FsubParams&, cudaStream_t);
   cudaError_t (*stage0)(const FsubParams&, cudaStream_t);
   cudaError_t (*update)(const UpdParams&, cudaStream_t);
+  cudaError_t (*batch)(const BatchParams&, int blocks, int threads, cudaStream_t);
+  int (*batch_occupancy)(int threads);  // resident blocks per SM
 };
 
 const KernelTable* kernels_for(int K, int C);

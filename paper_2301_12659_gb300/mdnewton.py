@@ -30,7 +30,10 @@ MDN_MAX_DEGREE = 63
 
 EXPORTS = ("mdn_create", "mdn_workspace_bytes", "mdn_load_system", "mdn_set_series", "mdn_newton",
            "mdn_get_series", "mdn_get_residual", "mdn_evaluate", "mdn_solve", "mdn_profile",
-           "mdn_status_word", "mdn_last_error", "mdn_destroy", "mdn_evaluate_static")
+           "mdn_status_word", "mdn_last_error", "mdn_destroy", "mdn_evaluate_static", "mdn_set_late_updates",
+           "mdn_batch_create", "mdn_batch_workspace_bytes", "mdn_batch_load", "mdn_batch_evaluate",
+           "mdn_batch_solve", "mdn_batch_tiles", "mdn_batch_last_error", "mdn_batch_destroy")
+BATCH_CONVERGED, BATCH_SINGULAR, BATCH_NONFINITE = 1, 2, 4
 MDN_NUM_PHASES = 5
 PHASES = ("evaluate", "assemble", "qr", "forward", "update")
 
@@ -65,12 +68,24 @@ def load(path: str = None) -> ctypes.CDLL:
     L.mdn_solve.argtypes = [P, P, P, P]
     L.mdn_profile.argtypes = [P, I, P, P]
     L.mdn_status_word.argtypes = [P]
+    L.mdn_set_late_updates.argtypes = [P, I, I]
+    L.mdn_batch_create.argtypes = [ctypes.POINTER(P), I, I, I, P, P, P, I, I]
+    L.mdn_batch_workspace_bytes.argtypes = [P, P]
+    L.mdn_batch_workspace_bytes.restype = ctypes.c_size_t
+    L.mdn_batch_load.argtypes = [P, P, P, P, P, P, P, ctypes.c_size_t, P]
+    L.mdn_batch_evaluate.argtypes = [P, P, P]
+    L.mdn_batch_solve.argtypes = [P, P, P, I, D, P, P]
+    L.mdn_batch_tiles.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    L.mdn_batch_last_error.argtypes = [P]
+    L.mdn_batch_last_error.restype = ctypes.c_char_p
+    L.mdn_batch_destroy.argtypes = [P]
     L.mdn_evaluate_static.argtypes = [I, I, I, I, I, I, P, P, P, P, P, P, P, P]
     L.mdn_last_error.argtypes = [P]
     L.mdn_last_error.restype = ctypes.c_char_p
     L.mdn_destroy.argtypes = [P]
     for name in EXPORTS:
-        if name not in ("mdn_workspace_bytes", "mdn_last_error", "mdn_destroy"):
+        if name not in ("mdn_workspace_bytes", "mdn_last_error", "mdn_destroy", "mdn_batch_workspace_bytes",
+                        "mdn_batch_last_error", "mdn_batch_destroy"):
             getattr(L, name).restype = I
     _lib = L
     return L
@@ -174,6 +189,10 @@ def mdn_evaluate_static(limbs, is_complex, n, degree, n_monomials, n_var_refs, e
                                       ctypes.c_void_p(int(cuda_stream)))
 
 
+def mdn_set_late_updates(ctx, first_stage: int, limbs: int) -> int:
+    return load().mdn_set_late_updates(ctx, first_stage, limbs)
+
+
 def mdn_status_word(ctx) -> int:
     return load().mdn_status_word(ctx)
 
@@ -251,10 +270,160 @@ class Newton:
         _check(self.ctx, mdn_solve(self.ctx, A.contiguous(), b.contiguous(), dx))
         return dx
 
+    def set_late_updates(self, first_stage: int, limbs: int):
+        """Stages k >= first_stage form their right hand side updates in
+        `limbs` (= K/2) limbs; limbs = K switches the variant off."""
+        _check(self.ctx, mdn_set_late_updates(self.ctx, first_stage, limbs))
+
     def close(self):
         if self.ctx is not None:
             mdn_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batched systems ----------------------------------------------------------
+
+def _bcheck(b, status: int):
+    if status != MDN_OK:
+        raise MdnError(status, load().mdn_batch_last_error(b).decode())
+
+
+def mdn_batch_create(limbs: int, is_complex: int, n, degree, n_monomials, threads_per_block: int = 0,
+                     blocks_per_sm: int = 0):
+    h = ctypes.c_void_p()
+    an, pn = _host_i32(n)
+    ad, pd = _host_i32(degree)
+    am, pm = _host_i32(n_monomials)
+    st = load().mdn_batch_create(ctypes.byref(h), int(limbs), int(is_complex), int(an.size), pn, pd, pm,
+                                 int(threads_per_block), int(blocks_per_sm))
+    if st != MDN_OK:
+        raise MdnError(st, "mdn_batch_create")
+    return h
+
+
+def mdn_batch_workspace_bytes(b, var_ptr) -> int:
+    a, p = _host_i32(var_ptr)
+    return int(load().mdn_batch_workspace_bytes(b, p))
+
+
+def mdn_batch_load(b, eq_of_monomial, var_ptr, var_idx, coeff, const_term, workspace, ws_bytes, cuda_stream) -> int:
+    aeq, peq = _host_i32(eq_of_monomial)
+    avp, pvp = _host_i32(var_ptr)
+    avi, pvi = _host_i32(var_idx)
+    return load().mdn_batch_load(b, peq, pvp, pvi, _ptr(coeff), _ptr(const_term),
+                                 ctypes.c_void_p(workspace.data_ptr()), int(ws_bytes),
+                                 ctypes.c_void_p(int(cuda_stream)))
+
+
+def mdn_batch_evaluate(b, x, f_out) -> int:
+    return load().mdn_batch_evaluate(b, _ptr(x), _ptr(f_out))
+
+
+def mdn_batch_solve(b, x0, x, max_steps: int, tol: float, steps_out, flags_out) -> int:
+    """steps_out, flags_out: host int32 arrays of the batch's count."""
+    assert steps_out.dtype == np.int32 and flags_out.dtype == np.int32
+    return load().mdn_batch_solve(b, _ptr(x0), _ptr(x), int(max_steps), float(tol),
+                                  steps_out.ctypes.data_as(ctypes.c_void_p), flags_out.ctypes.data_as(ctypes.c_void_p))
+
+
+def mdn_batch_tiles(b):
+    t, k = ctypes.c_int(0), ctypes.c_int(0)
+    st = load().mdn_batch_tiles(b, ctypes.byref(t), ctypes.byref(k))
+    return st, t.value, k.value
+
+
+def mdn_batch_last_error(b) -> str:
+    return load().mdn_batch_last_error(b).decode()
+
+
+def mdn_batch_destroy(b) -> None:
+    load().mdn_batch_destroy(b)
+
+
+class Batch:
+    """Many independent systems (one K and C) solved in one persistent
+    launch; see the mdn_batch_* calls of include/mdnewton.h.  Series of all
+    systems travel packed: the concatenation of the [K][C][n_s][d_s+1]
+    blocks."""
+
+    def __init__(self, systems, threads_per_block: int = 0, blocks_per_sm: int = 0, stream=None):
+        import torch
+
+        self.torch = torch
+        K, C = systems[0].K, systems[0].C
+        if any(s.K != K or s.C != C for s in systems):
+            raise ValueError("one K and C for the whole batch")
+        self.K, self.C, self.count = K, C, len(systems)
+        self.n = np.array([s.n for s in systems], dtype=np.int32)
+        self.deg = np.array([s.d for s in systems], dtype=np.int32)
+        self.M = np.array([s.M for s in systems], dtype=np.int32)
+        sizes = K * C * self.n.astype(np.int64) * (self.deg.astype(np.int64) + 1)
+        self.series_off = np.concatenate([[0], np.cumsum(sizes)])
+        eq = np.concatenate([s.eq for s in systems]).astype(np.int32)
+        nnz = np.array([s.vptr[-1] for s in systems], dtype=np.int64)
+        base = np.concatenate([[0], np.cumsum(nnz)[:-1]])
+        vptr = np.concatenate([s.vptr[:-1].astype(np.int64) + b0 for s, b0 in zip(systems, base)] +
+                              [np.array([nnz.sum()])]).astype(np.int32)
+        vidx = np.concatenate([s.vidx for s in systems]).astype(np.int32)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.dev = dev
+        self.stream = stream or torch.cuda.current_stream()
+        self.b = mdn_batch_create(K, C - 1, self.n, self.deg, self.M, threads_per_block, blocks_per_sm)
+        self.ws_bytes = mdn_batch_workspace_bytes(self.b, vptr)
+        if self.ws_bytes == 0:
+            raise MdnError(MDN_EINVAL, "mdn_batch_workspace_bytes")
+        ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=dev)
+        off = (-ws.data_ptr()) % 256
+        self.workspace = ws[off:off + self.ws_bytes]
+        self.coeff = torch.as_tensor(np.concatenate([np.ascontiguousarray(s.coeff).reshape(-1) for s in systems]),
+                                     device=dev)
+        self.cst = self.pack([s.cst if s.cst is not None else np.zeros((K, C, s.n, s.D)) for s in systems])
+        _bcheck(self.b, mdn_batch_load(self.b, eq, vptr, vidx, self.coeff, self.cst, self.workspace, self.ws_bytes,
+                                       self.stream.cuda_stream))
+
+    def pack(self, series):
+        """List of [K, C, n_s, d_s+1] arrays -> packed device tensor."""
+        flat = np.concatenate([np.ascontiguousarray(x, dtype=np.float64).reshape(-1) for x in series])
+        return self.torch.as_tensor(flat, device=self.dev)
+
+    def unpack(self, packed):
+        """Packed tensor -> list of host arrays [K, C, n_s, d_s+1]."""
+        h = packed.detach().cpu().numpy()
+        return [h[self.series_off[s]:self.series_off[s + 1]].reshape(self.K, self.C, int(self.n[s]),
+                                                                     int(self.deg[s]) + 1)
+                for s in range(self.count)]
+
+    def set_constant(self, packed):
+        self.cst.copy_(packed)
+
+    def tiles(self):
+        st, t, k = mdn_batch_tiles(self.b)
+        _bcheck(self.b, st)
+        return t, k
+
+    def evaluate(self, x):
+        f = self.torch.empty_like(x)
+        _bcheck(self.b, mdn_batch_evaluate(self.b, x, f))
+        return f
+
+    def solve(self, x0, max_steps: int, tol: float, x=None):
+        """Returns (x packed, steps [count], flags [count])."""
+        x = self.torch.empty_like(x0) if x is None else x
+        steps = np.zeros(self.count, dtype=np.int32)
+        flags = np.zeros(self.count, dtype=np.int32)
+        _bcheck(self.b, mdn_batch_solve(self.b, x0, x, max_steps, tol, steps, flags))
+        return x, steps, flags
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            mdn_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

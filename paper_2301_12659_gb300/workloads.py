@@ -250,3 +250,99 @@ def planted_system(cfg: PlantedConfig):
                   meta={"diag_monomials": np.asarray(diag_monomials, dtype=np.int32)})
     sysm.check()
     return sysm, xstar, x0
+
+
+# ---------------------------------------------------------------------------
+# batched homotopies: many independent planted systems of mixed size
+# ---------------------------------------------------------------------------
+@dataclass(frozen=True)
+class BatchConfig:
+    """`count` independent planted systems built like the quad double
+    workload (16 monomials per equation of U{2..8} distinct variables,
+    coefficients uniform in [-1, 1], diagonal term n*x_i, planted solution,
+    1e-3 noise on x_0), each with n drawn from `n_choices` and d from
+    `d_choices`; Newton stops by the batch stop rule with tolerance `tol`
+    or after `max_steps` updates."""
+
+    name: str
+    K: int
+    C: int
+    count: int
+    n_choices: tuple
+    d_choices: tuple
+    mono_per_eq: int = 16
+    kmin: int = 2
+    kmax: int = 8
+    max_steps: int = 12
+    tol: float = 1e-58
+    index: int = 3
+    noise: float = 1e-3
+
+    @property
+    def seed(self) -> int:
+        return BASE_SEED + self.index
+
+
+BATCH_CONFIGS = {
+    "qd-real-batch4096": BatchConfig("qd-real-batch4096", 4, 1, 4096, (8, 16, 32, 64), (7, 15, 31)),
+}
+
+
+def _uniform_int(u: np.ndarray, lo: int, hi: int) -> np.ndarray:
+    """Integers uniform in [lo, hi] from doubles u in [0, 1)."""
+    return lo + np.floor(u * (hi - lo + 1)).astype(np.int64)
+
+
+def batch_planted_systems(cfg: BatchConfig, count: Optional[int] = None):
+    """The systems of a batch (the first `count` of them): lists of
+    (System without cst, x*, x0).  System s draws from substreams of
+    substream_seed(cfg.seed, 1000 + s): its size class, then its monomials
+    (k uniform, the k distinct variables as the k smallest of n uniform
+    keys), coefficients, x* and the start noise; the diagonal monomial of
+    equation i follows its regular ones."""
+    count = cfg.count if count is None else count
+    K, C = cfg.K, cfg.C
+    out = []
+    for s in range(count):
+        seed = substream_seed(cfg.seed, 1000 + s)
+        u = 0.5 * (uniform_pm1(substream_seed(seed, 1), 2) + 1.0)
+        n = int(cfg.n_choices[int(u[0] * len(cfg.n_choices))])
+        d = int(cfg.d_choices[int(u[1] * len(cfg.d_choices))])
+        D = d + 1
+        mpe = cfg.mono_per_eq
+        kmax = min(cfg.kmax, n)
+        Mr = n * mpe
+        ku = 0.5 * (uniform_pm1(substream_seed(seed, 2), Mr) + 1.0)
+        k = _uniform_int(ku, cfg.kmin, kmax)
+        keys = uniform_pm1(substream_seed(seed, 3), Mr * n).reshape(Mr, n)
+        ranked = np.argsort(keys, axis=1, kind="stable")
+        sizes = np.empty(Mr + n, dtype=np.int64)
+        eq = np.empty(Mr + n, dtype=np.int32)
+        vlists = []
+        diag = []
+        mi = 0
+        for i in range(n):
+            for r in range(mpe):
+                m = i * mpe + r
+                sizes[mi] = k[m]
+                eq[mi] = i
+                vlists.append(ranked[m, :k[m]])
+                mi += 1
+            sizes[mi] = 1
+            eq[mi] = i
+            vlists.append(np.array([i]))
+            diag.append(mi)
+            mi += 1
+        vptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+        vidx = np.concatenate(vlists).astype(np.int32)
+        M = Mr + n
+        coeff = random_md((M, D), K, C, substream_seed(seed, 4))
+        coeff[:, :, diag, :] = 0.0
+        coeff[0, 0, diag, 0] = float(n)
+        xstar = random_md((n, D), K, C, substream_seed(seed, 5))
+        x0 = np.zeros((K, C, n, D))
+        x0[0, :, :, 0] = xstar[0, :, :, 0] + cfg.noise * uniform_pm1(substream_seed(seed, 6), C * n).reshape(C, n)
+        sysm = System(K, C, n, d, eq, vptr, vidx, coeff, None, f"{cfg.name}#{s}",
+                      meta={"diag_monomials": np.asarray(diag, dtype=np.int32)})
+        out.append((sysm, xstar, x0))
+    return out

@@ -10,7 +10,9 @@
   from the start series recovering the planted solution of the system whose
   constant term the library evaluates itself (a convergence property, not
   parity): x_0 and the leading coefficients to 1e-118, the error of x_0
-  squaring per step, the late coefficients to the conditioning floor.
+  squaring per step, the late coefficients to the conditioning floor; and
+  the same run with the stated-accuracy variant (updates of the stages
+  k >= 32 in quad double), which reaches the same accuracy.
 """
 import numpy as np
 import pytest
@@ -96,3 +98,25 @@ def test_od_complex_n128_d63(md):
     for a, b in zip(errs, errs[1:]):
         if a > 1e3 * cfg.tol:
             assert b <= max(1e4 * a * a, cfg.tol), errs
+
+
+def test_od_complex_n128_d63_late_updates(md):
+    """The stated-accuracy variant of the complex octo double workload: the
+    updates A_j dx_{k-j} of stages k >= (d+1)/2 = 32 in quad double.  The
+    residuals stay in octo double, so Newton reaches the plain run's accuracy
+    (x_0 and 16+ leading coefficients to 1e-118, the rest to the same
+    conditioning floor) with at most one extra step."""
+    cfg = wl.CONFIGS["od-complex-n128-d63"]
+    s, xstar, x0 = wl.planted_system(cfg)
+    s.cst = np.zeros((s.K, s.C, s.n, s.D))
+    nw = md.Newton(s)
+    cst = -nw.evaluate(xstar, want_A=False)
+    nw.set_constant(cst)
+    nw.set_late_updates(32, 4)
+    nw.set_series(x0)
+    nw.newton(cfg.steps + 1)
+    x = to_np(nw.series())
+    e = mt.series_rel_error(x, xstar)
+    assert np.max(e[:, 0]) <= cfg.tol
+    assert mt.correct_leading(x, xstar, cfg.tol) >= 16
+    assert np.max(e) <= 1e-100

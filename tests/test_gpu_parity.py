@@ -191,3 +191,54 @@ def test_newton_two_column_complex(md):
     nw.newton(8)
     x = to_np(nw.series())
     assert np.max(mt.series_rel_error(x, ts.solution_md(sol, 4, 2))) <= TOL[4]
+
+
+@pytest.mark.parametrize("K,C", [(8, 2), (8, 1), (4, 1), (2, 1)])
+def test_solve_late_updates_matches_oracle(md, K, C):
+    """Stated-accuracy variant: stages k >= 10 form their updates in K/2
+    limbs.  Early stages meet the K-limb tolerance against the oracle's
+    variant; late stages agree to the K/2-limb rounding level (the two sides
+    round the K/2-limb sums differently) and really differ from the plain
+    solve at that level."""
+    n, d, late = 9, 20, 10
+    A = wl.random_md((d + 1, n, n), K, C, 60 + K, unit_circle=False)
+    for i in range(n):
+        A[0, 0, 0, i, i] += n
+    b = wl.random_md((n, d + 1), K, C, 61 + K)
+    ref = oracle.solve(A, b, late=(late, K // 2))
+    cfg = wl.small_config(K, C, n=n, d=d, mono_per_eq=1, kmin=1, kmax=1, index=807)
+    s, _, _ = planted(cfg, with_cst=False)
+    nw = _newton(md, s)
+    nw.set_late_updates(late, K // 2)
+    dx = to_np(nw.solve(A, b))
+    eps_half = 2.0 ** (-52 * (K // 2))
+    e = mt.series_rel_error(dx, ref)
+    assert e[:, :late].max() <= TOL[K]
+    assert e[:, late:].max() <= 1e4 * eps_half
+    assert mt.series_rel_error(dx, oracle.solve(A, b))[:, late:].max() >= 1e-6 * eps_half
+    # switched off again: the plain solve
+    nw.set_late_updates(1, K)
+    assert np.max(mt.series_rel_error(to_np(nw.solve(A, b)), oracle.solve(A, b))) <= TOL[K]
+
+
+def test_set_late_updates_rejects_bad_arguments(md):
+    cfg = wl.small_config(4, 1, n=3, d=5, mono_per_eq=1, kmin=1, kmax=1, index=808)
+    s, _, _ = planted(cfg, with_cst=False)
+    nw = _newton(md, s)
+    for first, limbs in [(0, 2), (3, 3), (3, 1), (3, 8)]:
+        with pytest.raises(md.MdnError) as e:
+            nw.set_late_updates(first, limbs)
+        assert e.value.status == md.MDN_EINVAL
+
+
+def test_newton_late_updates_recovers_plant(md):
+    cfg = wl.small_config(8, 2, n=6, d=15, mono_per_eq=3, kmin=1, kmax=4, steps=9, index=506)
+    s, xstar, x0 = planted(cfg)
+    x_ref, _ = oracle.newton(s, x0, cfg.steps, late=(8, 4))
+    nw = _newton(md, s)
+    nw.set_late_updates(8, 4)
+    nw.set_series(x0)
+    nw.newton(cfg.steps)
+    x = to_np(nw.series())
+    assert np.max(mt.series_rel_error(x, xstar)) <= cfg.tol
+    assert np.max(mt.series_rel_error(x, x_ref)) <= cfg.tol

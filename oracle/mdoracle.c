@@ -611,7 +611,6 @@ static int back_sub(const qr_t *Q, const mdc *y, mdc *x) {
 /* Block lower triangular Toeplitz solve, Eq. (eqToeplitz)                    */
 /* ------------------------------------------------------------------------- */
 
-/* A [(d+1)][n][n], B and DX [n][d+1]: sum_{j<=k} A_j DX_{k-j} = B_k. */
 /* x rounded to L <= K limbs. */
 static void mdc_round_to(const mdc *x, int K, int C, int L, mdc *out) {
     cacc_t *t = (cacc_t *)malloc(sizeof(cacc_t));
@@ -621,6 +620,7 @@ static void mdc_round_to(const mdc *x, int K, int C, int L, mdc *out) {
     free(t);
 }
 
+/* A [(d+1)][n][n], B and DX [n][d+1]: sum_{j<=k} A_j DX_{k-j} = B_k. */
 /* Forward substitution of Section 5.4.  Stages k >= late_stage (the
  * stated-accuracy variant) form their update sum_{j>=1} A_j dx_{k-j} in
  * late_K limbs: every operand rounded to late_K limbs, the sum rounded to
@@ -934,6 +934,140 @@ int orc_newton_late(int K, int C, int n, int d, int M, const int32_t *eq, const 
     free(F);
     free(X);
     free(CS);
+    free(CF);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of the converged series (real systems)                             */
+/* ------------------------------------------------------------------------- */
+
+/* Fabry-ratio loss (the ratio theorem of Section 1.3: c_d / c_{d+1} of a
+ * series tends to its nearest singularity):
+ *   L = sum_i x_{i,d}^2 + x_{0,d-1} / x_{0,d},
+ * and g = dL/dx: 2 x_{i,d} at coefficient d of every variable, plus
+ * -x_{0,d-1} / x_{0,d}^2 there for variable 0 and 1 / x_{0,d} at its
+ * coefficient d-1; zero elsewhere.  Real data, d >= 1. */
+int orc_fabry_loss(int K, int n, int d, const double *x, double *loss, double *g) {
+    if (check_kc(K, 1) || n < 1 || d < 1) return ORC_EINVAL;
+    const long D = d + 1, N = (long)n * D;
+    mdc *X = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    mdc *G = (mdc *)calloc((size_t)N, sizeof(mdc));
+    soa_to_mdc(x, K, 1, N, X);
+    int rc = ORC_OK;
+    acc_t *s = (acc_t *)malloc(sizeof(acc_t));
+    acc_init(s);
+    for (int i = 0; i < n; ++i) {
+        const mdc *xd = &X[(size_t)i * D + d];
+        acc_add_prod(s, xd->re, xd->re, K, 1.0);
+        for (int l = 0; l < K; ++l) G[(size_t)i * D + d].re[l] = 2.0 * xd->re[l];
+    }
+    double ratio[KMAX] = {0}, inv[KMAX] = {0}, one[KMAX] = {1.0}, t[KMAX] = {0};
+    rc |= md_div_real(X[d - 1].re, X[d].re, K, ratio);
+    rc |= md_div_real(one, X[d].re, K, inv);
+    acc_add_md(s, ratio, K, 1.0);
+    double L[KMAX];
+    acc_round(s, K, L);
+    memcpy(G[d - 1].re, inv, sizeof(double) * K);
+    /* -ratio / x_{0,d} added to 2 x_{0,d} */
+    rc |= md_div_real(ratio, X[d].re, K, t);
+    acc_init(s);
+    acc_add_md(s, G[d].re, K, 1.0);
+    acc_add_md(s, t, K, -1.0);
+    acc_round(s, K, G[d].re);
+    for (int l = 0; l < K; ++l) loss[l] = L[l];
+    mdc_to_soa(G, K, 1, N, g);
+    free(s);
+    free(G);
+    free(X);
+    return rc;
+}
+
+/* Gradient of a loss of the converged series with respect to every
+ * coefficient series of the system.  At the solution f(x(c), c) = 0, so
+ * dL/dc = -lambda^T df/dc with J^T lambda = g, J the block lower triangular
+ * Toeplitz Jacobian of Eq. (eqToeplitz) (blocks A_0 .. A_d).  J^T is block
+ * upper triangular:
+ *   lambda_k = A_0^{-T} (g_k - sum_{j=1..d-k} A_j^T lambda_{k+j}),  k = d..0,
+ * with A_0^{-T} = Q R^{-T} from the Householder QR of A_0 (Section 5.3).
+ * Coefficient j of c_m enters f_{eq(m),k} through [t^{k-j}] p_m, p_m the
+ * product of the monomial's variables, so
+ *   grad c_{m,j} = -sum_{k=j..d} lambda_{eq(m),k} p_m[k-j]   (a correlation).
+ * x and g [K][1][n][d+1], grad [K][1][M][d+1]; real data. */
+int orc_adjoint(int K, int C, int n, int d, int M, const int32_t *eq, const int32_t *vptr,
+                const int32_t *vidx, const double *coeff, const double *x, const double *g, double *grad) {
+    if (check_kc(K, C) || C != 1 || check_structure(n, d, M, eq, vptr, vidx)) return ORC_EINVAL;
+    const long D = d + 1, N = (long)n * D;
+    mdc *CF = (mdc *)malloc(sizeof(mdc) * (size_t)(M > 0 ? M : 1) * D);
+    mdc *X = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    mdc *G = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    mdc *F = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    mdc *AA = (mdc *)malloc(sizeof(mdc) * (size_t)D * n * n);
+    mdc *LAM = (mdc *)calloc((size_t)N, sizeof(mdc));
+    mdc *GR = (mdc *)calloc((size_t)(M > 0 ? M : 1) * D, sizeof(mdc));
+    soa_to_mdc(coeff, K, C, (long)M * D, CF);
+    soa_to_mdc(x, K, C, N, X);
+    soa_to_mdc(g, K, C, N, G);
+    sys_t S = {K, C, n, d, M, eq, vptr, vidx, CF, NULL};
+    int rc = evaluate(&S, X, F, AA);
+    qr_t Q;
+    memset(&Q, 0, sizeof Q);
+    if (rc == ORC_OK) rc = qr_factor(AA, n, K, C, &Q);
+    if (rc == ORC_OK) {
+        mdc *r = (mdc *)malloc(sizeof(mdc) * (size_t)n);
+        mdc *y = (mdc *)malloc(sizeof(mdc) * (size_t)n);
+        cacc_t *t = (cacc_t *)malloc(sizeof(cacc_t));
+        for (int k = d; k >= 0 && rc == ORC_OK; --k) {
+            for (int i = 0; i < n; ++i) {
+                cacc_init(t);
+                cacc_add(t, &G[(size_t)i * D + k], K, C, 1.0);
+                for (int j = 1; j <= d - k; ++j)
+                    for (int l = 0; l < n; ++l)
+                        cacc_add_prod(t, &AA[((size_t)j * n + l) * n + i], &LAM[(size_t)l * D + k + j], K, C, -1.0);
+                cacc_round(t, K, C, &r[i]);
+            }
+            /* R^T y = r: forward substitution */
+            for (int i = 0; i < n; ++i) {
+                mdc num;
+                cacc_init(t);
+                cacc_add(t, &r[i], K, C, 1.0);
+                for (int l = 0; l < i; ++l) cacc_add_prod(t, &Q.R[(size_t)l * n + i], &y[l], K, C, -1.0);
+                cacc_round(t, K, C, &num);
+                rc |= mdc_div(&num, &Q.R[(size_t)i * n + i], K, C, &y[i]);
+            }
+            /* lambda_k = Q y = H_0 H_1 ... H_{n-1} y (real reflectors are symmetric) */
+            for (int j = n - 1; j >= 0; --j) qr_reflect(&Q, j, y);
+            for (int i = 0; i < n; ++i) LAM[(size_t)i * D + k] = y[i];
+        }
+        free(t);
+        free(y);
+        free(r);
+    }
+    if (rc == ORC_OK) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int m = 0; m < M; ++m) {
+            const int i = eq[m];
+            mdc *p = (mdc *)calloc((size_t)D, sizeof(mdc));
+            p[0].re[0] = 1.0;
+            for (int q = vptr[m]; q < vptr[m + 1]; ++q) series_mul(p, &X[(size_t)vidx[q] * D], p, d, K, C);
+            cacc_t *t = (cacc_t *)malloc(sizeof(cacc_t));
+            for (int j = 0; j < D; ++j) {
+                cacc_init(t);
+                for (int k = j; k < D; ++k) cacc_add_prod(t, &LAM[(size_t)i * D + k], &p[k - j], K, C, -1.0);
+                cacc_round(t, K, C, &GR[(size_t)m * D + j]);
+            }
+            free(t);
+            free(p);
+        }
+        mdc_to_soa(GR, K, C, (long)M * D, grad);
+    }
+    qr_free(&Q);
+    free(GR);
+    free(LAM);
+    free(AA);
+    free(F);
+    free(G);
+    free(X);
     free(CF);
     return rc;
 }

@@ -84,6 +84,18 @@ int orc_newton_late(int K, int C, int n, int d, int M, const int32_t *eq, const 
                     const int32_t *vidx, const double *coeff, const double *cst, const double *x0,
                     int steps, int late_stage, int late_K, double *x_out, double *hist);
 
+/* Fabry-ratio loss L = sum_i x_{i,d}^2 + x_{0,d-1} / x_{0,d} of a real series
+ * x [K][1][n][d+1] (d >= 1): loss [K] and g = dL/dx [K][1][n][d+1]. */
+int orc_fabry_loss(int K, int n, int d, const double *x, double *loss, double *g);
+
+/* Adjoint: gradient [K][1][M][d+1] of a loss with dL/dx = g with respect to
+ * the coefficient series of a real system, at a converged series x:
+ * lambda = J^{-T} g by the transposed block triangular solve with
+ * A_0^{-T} = Q R^{-T}, then grad c_{m,j} = -sum_{k>=j} lambda_{eq(m),k}
+ * [t^{k-j}] prod_{v in m} x_v. */
+int orc_adjoint(int K, int C, int n, int d, int M, const int32_t *eq, const int32_t *vptr,
+                const int32_t *vidx, const double *coeff, const double *x, const double *g, double *grad);
+
 #ifdef __cplusplus
 }
 #endif

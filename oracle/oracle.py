@@ -68,9 +68,11 @@ def lib():
             L.orc_newton.argtypes = [i, i, i, i, i, P, P, P, P, P, P, i, P, P]
             L.orc_solve_late.argtypes = [i, i, i, i, P, P, i, i, P]
             L.orc_newton_late.argtypes = [i, i, i, i, i, P, P, P, P, P, P, i, i, i, P, P]
+            L.orc_fabry_loss.argtypes = [i, i, i, P, P, P]
+            L.orc_adjoint.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P]
             for name in ("orc_md_binary", "orc_md_sqrt", "orc_series_mul", "orc_evaluate",
                          "orc_planted_constant", "orc_qr", "orc_solve", "orc_newton", "orc_solve_late",
-                         "orc_newton_late"):
+                         "orc_newton_late", "orc_fabry_loss", "orc_adjoint"):
                 getattr(L, name).restype = i
             _lib = L
     return _lib
@@ -195,3 +197,26 @@ def newton(sysm, x0, steps: int, late=None):
     _check(lib().orc_newton_late(K, C, n, d, M, _p(eq), _p(vptr), _p(vidx), _p(coeff), _p(cst), _p(x0),
                                  int(steps), ls, lk, _p(x), _p(hist)), "newton")
     return x, hist[:steps]
+
+
+def fabry_loss(x):
+    """L = sum_i x_{i,d}^2 + x_{0,d-1}/x_{0,d} of a real series x [K,1,n,d+1]:
+    returns (L as [K] limbs, g = dL/dx like x)."""
+    x = _f64(x)
+    K, C, n, D = x.shape
+    assert C == 1
+    loss = np.zeros(K)
+    g = np.zeros_like(x)
+    _check(lib().orc_fabry_loss(K, n, D - 1, _p(x), _p(loss), _p(g)), "fabry_loss")
+    return loss, g
+
+
+def adjoint(sysm, x, g) -> np.ndarray:
+    """Gradient [K,1,M,d+1] of a loss with dL/dx = g with respect to the
+    coefficient series of a real system, at the converged series x."""
+    K, C, n, d, M, eq, vptr, vidx, coeff = _sysargs(sysm)
+    x, g = _f64(x), _f64(g)
+    grad = np.zeros_like(coeff)
+    _check(lib().orc_adjoint(K, C, n, d, M, _p(eq), _p(vptr), _p(vidx), _p(coeff), _p(x), _p(g), _p(grad)),
+           "adjoint")
+    return grad

@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--e2e-solves", type=int, default=5)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", default="on", choices=["on", "off"],
+                    help="also time the batched workload (4096 quad double systems) and the same systems one by one")
+    ap.add_argument("--adjoint", default="on", choices=["on", "off"],
+                    help="also time the adjoint gradient of the double double n=64, d=31 workload")
+    ap.add_argument("--one-by-one-sample", type=int, default=48)
     ap.add_argument("--late-updates", type=int, default=0, metavar="FIRST_STAGE",
                     help="stated-accuracy variant: stages k >= FIRST_STAGE form their updates in K/2 limbs")
     return ap.parse_args()
@@ -192,6 +197,115 @@ def config_dict(cfg, args):
 
 
 # ---------------------------------------------------------------------------
+# the batched workload and the adjoint (extra objects of the JSON line)
+# ---------------------------------------------------------------------------
+def run_batched(args, dev):
+    """4096 independent quad double systems in one persistent launch (graph
+    replay), against the same systems solved one by one through mdn_newton
+    (a stratified sample, each run for the number of updates the batch gave
+    it, scaled by the class counts)."""
+    import torch
+    from paper_2301_12659_gb300 import autotune
+    from paper_2301_12659_gb300 import mdnewton as md
+
+    bcfg = wl.BATCH_CONFIGS["qd-real-batch4096"]
+    t0 = time.perf_counter()
+    items = wl.batch_planted_systems(bcfg)
+    gen_s = time.perf_counter() - t0
+    threads, bps, entry = autotune.batch_tiles(items, bcfg.max_steps, bcfg.tol)
+    systems = [s for s, _, _ in items]
+    b = md.Batch(systems, threads, bps)
+    b.set_constant(-b.evaluate(b.pack([xs for _, xs, _ in items])))
+    x0 = b.pack([x0 for _, _, x0 in items])
+    x = torch.empty_like(x0)
+    b.solve(x0, bcfg.max_steps, bcfg.tol, x)  # warm-up: captures the graph
+    times = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, steps, flags = b.solve(x0, bcfg.max_steps, bcfg.tol, x)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = min(times)
+    worst = 0.0
+    xs = b.unpack(x)
+    for q in range(0, len(items), 64):  # leading-limb spot check against the plant
+        worst = max(worst, float(np.max(np.abs(xs[q][0] - items[q][1][0]))))
+    cst = b.unpack(b.cst)
+    # one by one, on a stratified sample
+    idx = autotune._stratified(systems, args.one_by_one_sample, seed=1)
+    per_class = {}
+    for q in idx:
+        s = systems[q]
+        s.cst = cst[q]
+        nw = md.Newton(s)
+        nw.set_series(items[q][2])
+        nw.newton(max(1, int(steps[q])))
+        torch.cuda.synchronize()
+        nw.set_series(items[q][2])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        md.mdn_newton(nw.ctx, max(1, int(steps[q])), 0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        per_class.setdefault((s.n, s.d), []).append(e0.elapsed_time(e1))
+        nw.close()
+    counts = {}
+    for s in systems:
+        counts[(s.n, s.d)] = counts.get((s.n, s.d), 0) + 1
+    one_ms = sum(counts[c] * float(np.mean(v)) for c, v in per_class.items())
+    b.close()
+    return {
+        "workload": bcfg.name, "systems": len(items), "solves_per_s": len(items) / (ms * 1e-3),
+        "ms_per_batch": ms, "tiles": {"threads_per_block": threads, "blocks_per_sm": bps,
+                                      "source": "autotuner cache" if "timings" in entry else "tuned"},
+        "updates": int(np.sum(steps)), "converged": int(np.sum(flags == md.BATCH_CONVERGED)),
+        "max_leading_limb_error_vs_plant_sampled": worst, "gpu_launches_per_batch": 1,
+        "one_by_one": {"solves_per_s": len(items) / (one_ms * 1e-3), "ms_total_estimate": one_ms,
+                       "sample": f"{len(idx)} systems stratified by (n, d), each through mdn_newton for the "
+                                 "number of updates the batch applied to it, scaled by the class counts"},
+        "speedup_vs_one_by_one": one_ms / ms, "generate_s": gen_s,
+        "l2": "working set larger than L2 (GBs of Jacobians)",
+    }
+
+
+def run_adjoint(args, dev):
+    """Gradient of the Fabry-ratio loss of the converged dd n=64 d=31 series
+    with respect to every coefficient series (mdn_fabry_loss + mdn_adjoint)."""
+    import torch
+    from paper_2301_12659_gb300 import mdnewton as md
+
+    acfg = wl.ADJOINT_CONFIG
+    s, xstar, x0 = wl.planted_system(acfg)
+    s.cst = None
+    nw = md.Newton(s)
+    nw.set_constant(-nw.evaluate(xstar, want_A=False))
+    nw.set_series(x0)
+    nw.newton(acfg.steps)
+    x = nw.series()
+    loss, g = nw.fabry_loss(x)
+    grad = nw.adjoint(x, g)
+    torch.cuda.synchronize()
+    md.mdn_profile(nw.ctx, 1)
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        loss, g = nw.fabry_loss(x)
+        grad = nw.adjoint(x, g)
+    e1.record()
+    torch.cuda.synchronize()
+    _, phase_ms, _ = md.mdn_profile(nw.ctx, 0)
+    ms = e0.elapsed_time(e1) / reps
+    out = {"workload": acfg.name, "gradients_per_s": 1e3 / ms, "ms_per_gradient": ms,
+           "gradient_entries": int(grad.numel() // acfg.K), "loss_leading": float(loss[0]),
+           "phases_ms_per_gradient": {p: float(v) / reps for p, v in zip(md.PHASES, phase_ms)}}
+    nw.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args, cfg):
@@ -316,6 +430,10 @@ def run_ours(args, cfg):
         "check": {"max_leading_limb_error_vs_plant": diff, "final_norm_f": float(hist[-1, 0]) if hist is not None else None},
         "wall_s_timed_region": t_wall,
     }
+    if args.batched == "on":
+        line["batched"] = run_batched(args, dev)
+    if args.adjoint == "on":
+        line["adjoint"] = run_adjoint(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, cores = oracle_sample(cfg, args.cpu_sample_steps)
         line["cpu_baseline"] = {"value": args.cpu_sample_steps / dt, "unit": "steps/s", "cores": cores,

@@ -147,6 +147,36 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
  * later mdn_newton and mdn_solve calls on the context.  Default: off. */
 mdn_status mdn_set_late_updates(mdn_ctx* ctx, int first_stage, int limbs);
 
+/* Sampled residual monitor (Section 5.4 suggests the residuals of one or a
+ * few random equations instead of all of them): later mdn_newton calls form
+ * the monitor ||b - A dx||_1 on the `count` distinct rows listed (host
+ * array, 0 <= rows[q] < n) and scale it by n / count, saving the A_0 dx_k
+ * products of the other rows.  count = 0 (or n) restores all rows.  The
+ * caller picks the rows (e.g. at random). */
+mdn_status mdn_set_residual_rows(mdn_ctx* ctx, const int32_t* rows, int count);
+
+/* Adjoint of the converged series (real systems).  At a solution,
+ * f(x(c), c) = 0 mod t^{d+1}, so the gradient of a loss L(x) with respect to
+ * the coefficient series is dL/dc = -lambda^T df/dc with J^T lambda = dL/dx,
+ * J the block lower triangular Jacobian of Eq. (eqToeplitz) at x.  J^T is
+ * block upper triangular: lambda_k = A_0^{-T} (g_k - sum_{j>=1} A_j^T
+ * lambda_{k+j}) for k = d..0, with A_0^{-T} from the Householder QR of A_0
+ * (Section 5.3); then grad c_{m,j} = -sum_{k>=j} lambda_{eq(m),k}
+ * [t^{k-j}] prod_{v in m} x_v (the products are recomputed).
+ *   x: device [K][1][n][d+1], the series (normally mdn_newton's result);
+ *   g: device [K][1][n][d+1], dL/dx as md values;
+ *   grad_out: device [K][1][M][d+1].
+ * MDN_EINVAL for complex data; MDN_ESINGULAR for a zero pivot of A_0.
+ * Synchronises.  Overwrites the context's Jacobian and W (not x). */
+mdn_status mdn_adjoint(mdn_ctx* ctx, const double* x, const double* g, double* grad_out);
+
+/* The Fabry-ratio loss of a real series (Section 1.3: c_d / c_{d+1} of a
+ * series tends to its nearest singularity),
+ *   L = sum_i x_{i,d}^2 + x_{0,d-1} / x_{0,d},
+ * into loss_out (device [K] limbs) and g_out = dL/dx (device
+ * [K][1][n][d+1]).  Needs degree >= 1.  Enqueued on the context's stream. */
+mdn_status mdn_fabry_loss(mdn_ctx* ctx, const double* x, double* loss_out, double* g_out);
+
 /* Phases of a Newton step for mdn_profile(), after the kernel types of the
  * paper's Table 3 (Section 6.2): evaluation and differentiation
  * ("convolutions"), assembly of f and A, Householder QR with Q^H and back

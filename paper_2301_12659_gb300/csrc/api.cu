@@ -67,7 +67,7 @@ __global__ void norms_kernel(NormParams p) {
   }
   if (t == 0) {
     p.hist[0] = sh[0][0];
-    p.hist[1] = sh[1][0];
+    p.hist[1] = sh[1][0] * p.res_scale;
     p.hist[2] = sh[2][0];
   }
 }
@@ -166,6 +166,7 @@ struct Layout {
   size_t total = 0;
   size_t o_order, o_mono_k, o_mono_vp, o_mono_sbase, o_vidx, o_sched, o_sched_off, o_sched_nw, o_eq_ptr,
       o_eq_mon, o_pair_ptr, o_pair_slot, o_occ, o_counter, o_status, o_flags, o_epoch, o_done;
+  size_t o_mono_eq, o_adj, o_resmask;
   size_t o_x, o_f, o_dx, o_r, o_out, o_out0, o_scratch, o_A, o_A0b, o_Rm, o_Vm, o_Y, o_Z, o_W, o_xn0, o_tau, o_rinv, o_salpha, o_v0, o_fabs, o_dxabs,
       o_resabs, o_hist;
 };
@@ -177,11 +178,12 @@ struct mdn_ctx {
   int P = 1, G = 1;
   // system (host tables)
   int M = 0, nnz = 0, S = 0, kmax = 1, Smax = 1;
-  std::vector<int> order, mono_k, mono_vp, mono_sbase, vidx, sched_off, sched_nw, eq_ptr, eq_mon, pair_ptr,
+  std::vector<int> order, mono_k, mono_vp, mono_sbase, mono_eq, vidx, sched_off, sched_nw, eq_ptr, eq_mon, pair_ptr,
       pair_slot, occ;
   std::vector<int4> sched;
   bool loaded = false, has_series = false;
   int late_stage = 1 << 30;  // stages from here form their updates in K/2 limbs
+  int res_rows = 0;          // rows of the sampled residual monitor (0: all)
   const double* coeff = nullptr;
   const double* cst = nullptr;
   cudaStream_t stream = nullptr;
@@ -297,6 +299,7 @@ static mdn_status build_tables(mdn_ctx* ctx, int M, const int32_t* eq, const int
     for (int q = 0; q < ctx->nnz; ++q)
       if (vidx[q] < 0 || vidx[q] >= n) return fail(ctx, MDN_EINVAL, "var_idx[%d] = %d out of range", q, vidx[q]);
     ctx->vidx.assign(vidx, vidx + ctx->nnz);
+    ctx->mono_eq.assign(eq, eq + M);
     ctx->occ.assign(ctx->nnz, 0);
     for (int m = 0; m < M; ++m)
       for (int q = vptr[m]; q < vptr[m + 1]; ++q) ctx->occ[q] = m;
@@ -343,6 +346,7 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_mono_k = take(4 * M);
   L.o_mono_vp = take(4 * M);
   L.o_mono_sbase = take(4 * M);
+  L.o_mono_eq = take(4 * M);
   L.o_vidx = take(4 * (size_t)ctx->nnz);
   L.o_sched = take(sizeof(int4) * ctx->sched.size());
   L.o_sched_off = take(4 * ctx->sched_off.size());
@@ -365,6 +369,7 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_out = take(8 * KC * (size_t)ctx->S * D);
   L.o_out0 = take(8 * KC * (size_t)ctx->S);
   L.o_scratch = take(8 * KC * (size_t)ctx->Wtot * ctx->Smax * D);
+  L.o_adj = take(8 * KC * (size_t)ctx->Wtot * 2 * ctx->G * D);  // products of the adjoint
   L.o_A = take(8 * KC * D * n * n);
   L.o_A0b = take(8 * KC * n * n * 2);  // A_0 of this step and of the next (pipelined QR)
   L.o_Rm = take(8 * KC * n * n);
@@ -380,6 +385,7 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_fabs = take(8 * n * D);
   L.o_dxabs = take(8 * n * D);
   L.o_resabs = take(8 * n * D);
+  L.o_resmask = take(4 * n);
   L.o_hist = take(8 * 3 * MDN_MAX_STEPS);
   L.total = o;
 }
@@ -463,6 +469,7 @@ mdn_status mdn_load_system(mdn_ctx* ctx, int M, const int32_t* eq, const int32_t
   CU(put(L.o_mono_k, ctx->mono_k.data(), 4 * ctx->mono_k.size()));
   CU(put(L.o_mono_vp, ctx->mono_vp.data(), 4 * ctx->mono_vp.size()));
   CU(put(L.o_mono_sbase, ctx->mono_sbase.data(), 4 * ctx->mono_sbase.size()));
+  CU(put(L.o_mono_eq, ctx->mono_eq.data(), 4 * ctx->mono_eq.size()));
   CU(put(L.o_vidx, ctx->vidx.data(), 4 * ctx->vidx.size()));
   CU(put(L.o_sched, ctx->sched.data(), sizeof(int4) * ctx->sched.size()));
   CU(put(L.o_sched_off, ctx->sched_off.data(), 4 * ctx->sched_off.size()));
@@ -478,6 +485,7 @@ mdn_status mdn_load_system(mdn_ctx* ctx, int M, const int32_t* eq, const int32_t
   CU(cudaMemsetAsync(ctx->ws + L.o_epoch, 0, 4, st));
   CU(cudaMemsetAsync(ctx->ws + L.o_dx, 0, 8 * (size_t)ctx->K * ctx->C * ctx->n * ctx->D, st));
   CU(cudaStreamSynchronize(st));  // host tables may be reused after return
+  ctx->res_rows = 0;
   ctx->loaded = true;
   ctx->err.clear();
   return MDN_OK;
@@ -632,7 +640,8 @@ static int qr_blocks(const mdn_ctx* ctx) { return 3 * ((ctx->n + (QR_THREADS / 3
 // event e0 recorded after it when not null, then the remaining stages on
 // `blocks` SMs.
 static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, long long NA0, const double* W,
-                              const double* rhs, int sgn, double* dx, const double* x, cudaEvent_t e0, int blocks) {
+                              const double* rhs, int sgn, double* dx, const double* x, cudaEvent_t e0, int blocks,
+                              bool transposed = false) {
   const Layout& L = ctx->L;
   const long long D = ctx->D, n = ctx->n;
   ph_begin(ctx, MDN_PHASE_FORWARD);
@@ -644,7 +653,9 @@ static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, l
   u.nW = std::min(ctx->n, 4 * FSUB_WBLOCKS);
   const int wb = (u.nW + 3) / 4;
   u.nOwn = (int)std::min<long long>(4LL * std::max(1, blocks - wb), (long long)ctx->n * ctx->D);
-  u.late_stage = std::min(ctx->late_stage, ctx->D);
+  u.late_stage = transposed ? ctx->D : std::min(ctx->late_stage, ctx->D);
+  u.transpose = transposed ? 1 : 0;
+  u.reverse = transposed ? 1 : 0;
   u.A = A;
   u.NA = D * n * n;
   u.A0 = A0;
@@ -658,6 +669,7 @@ static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, l
   u.x = x;
   u.xnext0 = x ? ctx->at<double>(L.o_xn0) : nullptr;
   u.resabs = ctx->at<double>(L.o_resabs);
+  u.resmask = ctx->res_rows ? ctx->at<int>(L.o_resmask) : nullptr;
   u.rdone = ctx->at<unsigned>(L.o_done);
   u.xdone = u.rdone + ctx->D;
   u.status = ctx->at<int>(L.o_status);
@@ -741,6 +753,7 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
     np.count = n * D;
     np.fabs = u.fabs;
     np.resabs = ctx->at<double>(L.o_resabs);
+    np.res_scale = ctx->res_rows ? (double)ctx->n / ctx->res_rows : 1.0;
     np.dxabs = u.dxabs;
     np.hist = hist + 3 * s;
     norms_kernel<<<1, 1024, 0, ctx->stream>>>(np);
@@ -824,6 +837,89 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
   ph_end(ctx, MDN_PHASE_QR, 3);
   if ((r = run_forward(ctx, A, A, DNN, W, b, +1, dx, nullptr, nullptr, ctx->num_sms)) != MDN_OK) return r;
   return read_status(ctx);
+}
+
+mdn_status mdn_fabry_loss(mdn_ctx* ctx, const double* x, double* loss_out, double* g_out) {
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
+  if (!x || !loss_out || !g_out) return fail(ctx, MDN_EINVAL, "null pointer argument");
+  if (ctx->C != 1 || ctx->D < 2) return fail(ctx, MDN_EINVAL, "the loss needs real data and degree >= 1");
+  LossParams lp{};
+  lp.n = ctx->n;
+  lp.D = ctx->D;
+  lp.x = x;
+  lp.Nx = (long long)ctx->n * ctx->D;
+  lp.loss = loss_out;
+  lp.g = g_out;
+  CU(ctx->kt->fabry(lp, ctx->stream));
+  return MDN_OK;
+}
+
+// dL/dc = -lambda^T df/dc with J^T lambda = g (J the block lower triangular
+// Jacobian of Eq. (eqToeplitz) at x): A(t) and A_0^{-1} at x, the solve with
+// J^T as the forward substitution with transposed blocks in reversed stage
+// order (A_0^{-T} = W^T), then the correlations of the coefficient adjoints.
+mdn_status mdn_adjoint(mdn_ctx* ctx, const double* x, const double* g, double* grad_out) {
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
+  if (!x || !g || !grad_out) return fail(ctx, MDN_EINVAL, "null pointer argument");
+  if (ctx->C != 1) return fail(ctx, MDN_EINVAL, "the adjoint is defined for real data");
+  const Layout& L = ctx->L;
+  const long long n = ctx->n, D = ctx->D, DNN = D * n * n;
+  CU(cudaMemsetAsync(ctx->at<int>(L.o_status), 0, 4, ctx->stream));
+  double* A = ctx->at<double>(L.o_A);
+  double* f = ctx->at<double>(L.o_f);
+  double* W = ctx->at<double>(L.o_W);
+  double* lam = ctx->at<double>(L.o_dx);
+  mdn_status r;
+  if ((r = run_a0(ctx, x, n * D, ctx->D, A, DNN, ctx->stream)) != MDN_OK) return r;
+  if ((r = run_evaluate(ctx, x, f, A, ctx->num_sms)) != MDN_OK) return r;
+  ph_begin(ctx, MDN_PHASE_QR);
+  if ((r = run_qr(ctx, A, DNN, W, ctx->stream)) != MDN_OK) return r;
+  ph_end(ctx, MDN_PHASE_QR, 3);
+  if ((r = run_forward(ctx, A, A, DNN, W, g, +1, lam, nullptr, nullptr, ctx->num_sms, true)) != MDN_OK) return r;
+  AdjParams a{};
+  a.n = ctx->n;
+  a.D = ctx->D;
+  a.M = ctx->M;
+  a.P = ctx->P;
+  a.G = ctx->G;
+  a.Wtot = ctx->Wtot;
+  a.mono_eq = ctx->at<int>(L.o_mono_eq);
+  a.mono_vp = ctx->at<int>(L.o_mono_vp);
+  a.mono_k = ctx->at<int>(L.o_mono_k);
+  a.vidx = ctx->at<int>(L.o_vidx);
+  a.x = x;
+  a.Nx = n * D;
+  a.lam = lam;
+  a.grad = grad_out;
+  a.Ng = (long long)ctx->M * D;
+  a.scratch = ctx->at<double>(L.o_adj);
+  a.Ns = (long long)ctx->Wtot * 2 * ctx->G * D;
+  ph_begin(ctx, MDN_PHASE_EVALUATE);
+  CU(ctx->kt->adjoint(a, ctx->stream));
+  ph_end(ctx, MDN_PHASE_EVALUATE, 1);
+  return read_status(ctx);
+}
+
+mdn_status mdn_set_residual_rows(mdn_ctx* ctx, const int32_t* rows, int count) {
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
+  if (count < 0 || count > ctx->n || (count > 0 && !rows)) return fail(ctx, MDN_EINVAL, "bad row count");
+  std::vector<int> mask(ctx->n, count ? 0 : 1);
+  for (int q = 0; q < count; ++q) {
+    if (rows[q] < 0 || rows[q] >= ctx->n) return fail(ctx, MDN_EINVAL, "row %d out of range", rows[q]);
+    if (mask[rows[q]]) return fail(ctx, MDN_EINVAL, "row %d listed twice", rows[q]);
+    mask[rows[q]] = 1;
+  }
+  const Layout& L = ctx->L;
+  CU(cudaMemcpyAsync(ctx->at<int>(L.o_resmask), mask.data(), 4 * (size_t)ctx->n, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  // rows outside the sample contribute zero to the monitor
+  CU(cudaMemsetAsync(ctx->at<double>(L.o_resabs), 0, 8 * (size_t)ctx->n * ctx->D, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->res_rows = (count == ctx->n) ? 0 : count;
+  return MDN_OK;
 }
 
 mdn_status mdn_set_late_updates(mdn_ctx* ctx, int first_stage, int limbs) {

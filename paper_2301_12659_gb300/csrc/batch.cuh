@@ -451,8 +451,9 @@ __global__ void batch_kernel(BatchParams p) {
     }
     int flags = 0, steps = 0;
     for (;;) {
-      batch_evaluate<K, C>(p, s, w, w.f, N, true);
+      __syncthreads();  // every thread has read the norms of the last step
       if (tid < 3) s_max[tid] = 0ull;
+      batch_evaluate<K, C>(p, s, w, w.f, N, true);
       __syncthreads();
       // ||f||_inf, and a non-finite check of f
       unsigned long long fm = 0;
@@ -537,7 +538,8 @@ template <int K, int C>
 const KernelTable* make_table() {
   static const KernelTable t = {K, C, &launch_ed<K, C>, &launch_a0<K, C>, &ed_blocks_per_sm<K, C>, &launch_assemble<K, C>,
                                 &launch_qr<K, C>, &launch_fsub<K, C>, &launch_stage0<K, C>,
-                                &launch_update<K, C>, &launch_batch<K, C>, &batch_occupancy<K, C>};
+                                &launch_update<K, C>, &launch_adjoint<K, C>, &launch_fabry<K, C>,
+                                &launch_batch<K, C>, &batch_occupancy<K, C>};
   return &t;
 }
 

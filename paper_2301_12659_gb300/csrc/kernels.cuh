@@ -725,17 +725,18 @@ __device__ __forceinline__ void st_acc(double* p, long long N, long long i, cons
   st(p, N, i, v);
 }
 
-// (M x)[i] over the warp for a row-major n-by-n block M and a column of
-// series coefficients x (coefficient kx of every variable); all lanes get it.
+// sum_l M[row_off + l*ms] x_l over the warp (a row of a row-major n-by-n
+// block for ms = 1, a column for ms = n) with x_l = coefficient kx of
+// variable l; all lanes get it.
 template <int K, int C>
-__device__ __forceinline__ void warp_rowdot(const double* Mp, long long NM, long long row_off, const double* xp,
-                                            long long Nx, int n, int D, int kx, cmd<K, C>& out) {
+__device__ __forceinline__ void warp_rowdot(const double* Mp, long long NM, long long row_off, int ms,
+                                            const double* xp, long long Nx, int n, int D, int kx, cmd<K, C>& out) {
   const int lane = threadIdx.x & 31;
   CAcc<K, C> acc;
   cacc_zero(acc);
   for (int l = lane; l < n; l += 32) {
     cmd<K, C> a, x;
-    ld(Mp, NM, row_off + l, a);
+    ld(Mp, NM, row_off + (long long)l * ms, a);
     ld(xp, Nx, (long long)l * D + kx, x);
     cacc_fma(acc, a, x);
   }
@@ -748,6 +749,11 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
   const int n = p.n, D = p.D;
   const long long nn = (long long)n * n;
   const int wblocks = (p.nW + 3) / 4;
+  // transposed blocks: row i of M^T is column i of M; reversed stages: stage
+  // k works on coefficient D-1-k of the series
+  const int ms = p.transpose ? n : 1;
+  auto row = [&](long long base, int i) { return base + (p.transpose ? (long long)i : (long long)i * n); };
+  auto co = [&](int k) { return p.reverse ? D - 1 - k : k; };
   if ((int)blockIdx.x < wblocks) {
     // ---- solve warps: dx_k = W r_k ----
     const int w = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -756,8 +762,8 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
       if (!warp_wait(&p.rdone[k], (unsigned)n, p.spin_limit, p.status)) return;
       for (int i = w; i < n; i += p.nW) {
         cmd<K, C> s;
-        warp_rowdot<K, C>(p.W, p.Nnn, (long long)i * n, p.r, p.Nx, n, D, k, s);
-        if (lane == 0) st(p.dx, p.Nx, (long long)i * D + k, s);
+        warp_rowdot<K, C>(p.W, p.Nnn, row(0, i), ms, p.r, p.Nx, n, D, co(k), s);
+        if (lane == 0) st(p.dx, p.Nx, (long long)i * D + co(k), s);
         warp_count(&p.xdone[k]);
       }
     }
@@ -773,12 +779,12 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
     const int k = (int)(q / n), i = (int)(q - (long long)k * n);
     if (k < p.first_stage) continue;  // r_0 stored by stage0_kernel
     cmd<K, C> b;
-    ld(p.rhs, p.Nx, (long long)i * D + k, b);
+    ld(p.rhs, p.Nx, (long long)i * D + co(k), b);
     if (p.rhs_sign < 0) {
       md_neg(b.re, b.re);
       md_neg(b.im, b.im);
     }
-    if (lane == 0) st(p.r, p.Nx, (long long)i * D + k, b);
+    if (lane == 0) st(p.r, p.Nx, (long long)i * D + co(k), b);
     if (k == 0) {
       __syncwarp();
       warp_count(&p.rdone[0]);
@@ -801,7 +807,7 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
           // the leading K/2 doubles of A and dx are K/2-limb values (limb
           // index outermost in the layout): the same pointers and strides
           cmd<K / 2, C> h;
-          warp_rowdot<K / 2, C>(p.A, p.NA, (long long)(k - m) * nn + (long long)i * n, p.dx, p.Nx, n, D, m, h);
+          warp_rowdot<K / 2, C>(p.A, p.NA, row((long long)(k - m) * nn, i), ms, p.dx, p.Nx, n, D, co(m), h);
           cmd_zero(ax);
 #pragma unroll
           for (int l = 0; l < K / 2; ++l) {
@@ -809,34 +815,35 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
             ax.im[l] = h.im[l];
           }
         } else {
-          warp_rowdot<K, C>(p.A, p.NA, (long long)(k - m) * nn + (long long)i * n, p.dx, p.Nx, n, D, m, ax);
+          warp_rowdot<K, C>(p.A, p.NA, row((long long)(k - m) * nn, i), ms, p.dx, p.Nx, n, D, co(m), ax);
         }
       } else {
-        warp_rowdot<K, C>(p.A, p.NA, (long long)(k - m) * nn + (long long)i * n, p.dx, p.Nx, n, D, m, ax);
+        warp_rowdot<K, C>(p.A, p.NA, row((long long)(k - m) * nn, i), ms, p.dx, p.Nx, n, D, co(m), ax);
       }
       CAcc<K, C> a;
-      ld_acc(p.r, p.Nx, (long long)i * D + k, a);
+      ld_acc(p.r, p.Nx, (long long)i * D + co(k), a);
       cacc_add(a, ax, -1.0);
       if (k == m + 1) {
         cmd<K, C> r;
         cacc_get(a, r);
-        if (lane == 0) st(p.r, p.Nx, (long long)i * D + k, r);
+        if (lane == 0) st(p.r, p.Nx, (long long)i * D + co(k), r);
         __syncwarp();
         warp_count(&p.rdone[k]);
       } else {
-        if (lane == 0) st_acc(p.r, p.Nx, (long long)i * D + k, a);
+        if (lane == 0) st_acc(p.r, p.Nx, (long long)i * D + co(k), a);
         __syncwarp();
       }
     }
     for (long long q = ow; q < items; q += p.nOwn) {
       const int k = (int)(q / n), i = (int)(q - (long long)k * n);
       if (k != m) continue;
+      if (p.resmask && !p.resmask[i]) continue;  // a row outside the sampled monitor
       // residual of stage m: r_m[i] - (A_0 dx_m)[i]
       cmd<K, C> ax, r, res;
-      warp_rowdot<K, C>(p.A0, p.NA0, (long long)i * n, p.dx, p.Nx, n, D, m, ax);
-      ld(p.r, p.Nx, (long long)i * D + k, r);
+      warp_rowdot<K, C>(p.A0, p.NA0, row(0, i), ms, p.dx, p.Nx, n, D, co(m), ax);
+      ld(p.r, p.Nx, (long long)i * D + co(k), r);
       cmd_sub(r, ax, res);
-      if (lane == 0) p.resabs[(long long)i * D + m] = (C == 2) ? hypot(res.re[0], res.im[0]) : fabs(res.re[0]);
+      if (lane == 0) p.resabs[(long long)i * D + co(m)] = (C == 2) ? hypot(res.re[0], res.im[0]) : fabs(res.re[0]);
     }
   }
 }
@@ -850,12 +857,13 @@ __global__ void stage0_kernel(FsubParams p) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int n = p.n, D = p.D;
   if (i >= n) return;
+  const int c0 = p.reverse ? D - 1 : 0;  // coefficient of stage 0
   CAcc<K, C> acc;
   cacc_zero(acc);
   for (int l = lane; l < n; l += 32) {
     cmd<K, C> w, b;
-    ld(p.W, p.Nnn, (long long)i * n + l, w);
-    ld(p.rhs, p.Nx, (long long)l * D, b);
+    ld(p.W, p.Nnn, p.transpose ? (long long)l * n + i : (long long)i * n + l, w);
+    ld(p.rhs, p.Nx, (long long)l * D + c0, b);
     cacc_fma(acc, w, b);
   }
   cmd<K, C> s;
@@ -866,13 +874,13 @@ __global__ void stage0_kernel(FsubParams p) {
   }
   if (lane == 0) {
     cmd<K, C> b;
-    ld(p.rhs, p.Nx, (long long)i * D, b);
+    ld(p.rhs, p.Nx, (long long)i * D + c0, b);
     if (p.rhs_sign < 0) {
       md_neg(b.re, b.re);
       md_neg(b.im, b.im);
     }
-    st(p.r, p.Nx, (long long)i * D, b);
-    st(p.dx, p.Nx, (long long)i * D, s);
+    st(p.r, p.Nx, (long long)i * D + c0, b);
+    st(p.dx, p.Nx, (long long)i * D + c0, s);
     if (p.xnext0) {
       cmd<K, C> x0, xn;
       ld(p.x, p.Nx, (long long)i * D, x0);
@@ -905,6 +913,117 @@ __global__ void update_kernel(UpdParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint of the coefficient series (real data)
+// ---------------------------------------------------------------------------
+// Lane group g of warp wg takes monomial m = wg*G + g (+ multiples of
+// Wtot*G): p_m = prod_v x_v by forward products (ping-pong in its two scratch
+// series), then the correlation with lambda of its equation; lane t forms
+// coefficients j1 = t (D-t terms) and j2 = D-1-t (t+1 terms), D+1 multiply-
+// adds in one loop with the accumulator picked by select.
+template <int K, int C>
+__global__ void adj_coeff_kernel(AdjParams p) {
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wg >= p.Wtot) return;
+  const int D = p.D, P = p.P, G = p.G;
+  const int g = lane / P, t = lane - g * P;
+  const bool ingroup = g < G;
+  for (int base = wg * G; base < p.M; base += p.Wtot * G) {
+    const int m = base + g;
+    const bool act = ingroup && m < p.M;
+    const int k = act ? p.mono_k[m] : 0;
+    const int vp = act ? p.mono_vp[m] : 0;
+    int kw = k;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) kw = max(kw, __shfl_xor_sync(FULL, kw, off));
+    const long long s0 = ((long long)wg * G + (ingroup ? g : 0)) * 2;
+    SP cur{const_cast<double*>(p.x), p.Nx, act ? (long long)p.vidx[vp] * D : 0};
+    for (int q = 2; q <= kw; ++q) {
+      SP o{p.scratch, p.Ns, (s0 + (q & 1)) * D};
+      if (act && q <= k) {
+        SP b{const_cast<double*>(p.x), p.Nx, (long long)p.vidx[vp + q - 1] * D};
+        series_product<K, C>(cur, b, o, t, D);
+        cur = o;
+      }
+      __syncwarp();
+    }
+    if (act) {
+      const int i = p.mono_eq[m];
+      const int j1 = t, j2 = D - 1 - t;
+      CAcc<K, C> acc1, acc2;
+      cacc_zero(acc1);
+      cacc_zero(acc2);
+      for (int s = 0; s <= D; ++s) {
+        const bool first = s < D - t;
+        const int kk = first ? j1 + s : j2 + (s - (D - t));
+        const int pj = first ? s : s - (D - t);
+        cmd<K, C> lv, pv;
+        ld(p.lam, p.Nx, (long long)i * D + kk, lv);
+        ld(cur.p, cur.N, cur.off + pj, pv);
+        CAcc<K, C> acc;
+        cacc_select(first, acc1, acc2, acc);
+        cacc_fma(acc, lv, pv);
+        cacc_select(first, acc, acc1, acc1);
+        cacc_select(first, acc2, acc, acc2);
+      }
+      cmd<K, C> r1, r2;
+      cacc_get(acc1, r1);
+      cacc_get(acc2, r2);
+      md_neg(r1.re, r1.re);
+      md_neg(r1.im, r1.im);
+      md_neg(r2.re, r2.re);
+      md_neg(r2.im, r2.im);
+      st(p.grad, p.Ng, (long long)m * D + j1, r1);
+      if (j2 != j1) st(p.grad, p.Ng, (long long)m * D + j2, r2);
+    }
+    __syncwarp();
+  }
+}
+
+// L = sum_i x_{i,d}^2 + x_{0,d-1} / x_{0,d} and g = dL/dx (one block; real data,
+// D >= 2): 2 x_{i,d} at coefficient d, minus x_{0,d-1} / x_{0,d}^2 for
+// variable 0, and 1 / x_{0,d} at its coefficient d-1.
+template <int K>
+__global__ void fabry_kernel(LossParams p) {
+  const int n = p.n, D = p.D, d = D - 1;
+  for (long long e = threadIdx.x; e < (long long)n * D; e += blockDim.x) {
+    double v[K];
+    ld_real(p.x, p.Nx, e, v);
+    const bool last = (e % D) == d;
+#pragma unroll
+    for (int l = 0; l < K; ++l) v[l] = last ? 2.0 * v[l] : 0.0;
+    st_real(p.g, p.Nx, e, v);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Acc<K> s;
+    acc_zero(s);
+    double xd[K], xm[K], ratio[K], inv[K], t[K], g0[K], one[K];
+    for (int i = 0; i < n; ++i) {
+      ld_real(p.x, p.Nx, (long long)i * D + d, xd);
+      acc_fma(s, xd, xd);
+    }
+    ld_real(p.x, p.Nx, d, xd);
+    ld_real(p.x, p.Nx, d - 1, xm);
+    md_zero(one);
+    one[0] = 1.0;
+    md_div(xm, xd, ratio);
+    md_recip(xd, inv);
+    acc_add(s, ratio, 1.0);
+    double L[K];
+    acc_get(s, L);
+    md_mul(ratio, inv, t);
+    ld_real(p.g, p.Nx, d, g0);
+    md_sub(g0, t, g0);
+    st_real(p.g, p.Nx, d, g0);
+    st_real(p.g, p.Nx, d - 1, inv);
+#pragma unroll
+    for (int l = 0; l < K; ++l) p.loss[l] = L[l];
+    (void)one;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers of one (K, C) instantiation
 // ---------------------------------------------------------------------------
 inline int grid_for(long long work, int threads) {
@@ -912,6 +1031,17 @@ inline int grid_for(long long work, int threads) {
   if (g < 1) g = 1;
   if (g > 8192) g = 8192;
   return (int)g;
+}
+template <int K, int C>
+cudaError_t launch_adjoint(const AdjParams& p, cudaStream_t s) {
+  const int warps = 4;
+  adj_coeff_kernel<K, C><<<(p.Wtot + warps - 1) / warps, 32 * warps, 0, s>>>(p);
+  return cudaGetLastError();
+}
+template <int K, int C>
+cudaError_t launch_fabry(const LossParams& p, cudaStream_t s) {
+  fabry_kernel<K><<<1, 256, 0, s>>>(p);
+  return cudaGetLastError();
 }
 template <int K, int C>
 cudaError_t launch_ed(const EdParams& p, int grid, cudaStream_t s) {

@@ -108,6 +108,9 @@ struct FsubParams {
   int nW;       // solve warps (dx_k = W r_k), on the first nW/4 blocks
   int nOwn;     // owner warps of the r_k[i] accumulators
   int late_stage;  // stages k >= late_stage form their updates in K/2 limbs (D: never)
+  const int* resmask;  // rows whose residual the monitor forms (null: all)
+  int transpose;   // 1: use A_j^T and W^T (the adjoint's solve with J^T)
+  int reverse;     // 1: stage k works on coefficient D-1-k (J^T is block upper triangular)
   const double* A;
   long long NA;  // D*n*n (slices j >= 1 are read)
   const double* A0;
@@ -143,10 +146,35 @@ struct NormParams {
   const double* fabs;
   const double* resabs;
   const double* dxabs;
+  double res_scale;  // n / sampled rows of the residual monitor
   double* hist;  // 3 values
 };
 
 // Launchers of one (K, C) instantiation.
+// Adjoint of the coefficient series: grad[m][j] = -sum_{k>=j} lam_{eq(m),k} [t^{k-j}] prod x_v.
+struct AdjParams {
+  int n, D, M, P, G, Wtot;
+  const int* mono_eq;
+  const int* mono_vp;
+  const int* mono_k;
+  const int* vidx;
+  const double* x;
+  long long Nx;      // n*D
+  const double* lam;
+  double* grad;      // [K][C][M][D]
+  long long Ng;      // M*D
+  double* scratch;   // per warp 2*G series of D
+  long long Ns;
+};
+// Fabry-ratio loss of a real series and its gradient.
+struct LossParams {
+  int n, D;
+  const double* x;
+  long long Nx;
+  double* loss;  // [K]
+  double* g;     // [K][1][n][D]
+};
+
 // ---- batched systems (one persistent launch) ----
 struct BatchSys {
   int n, D, M, mono0;      // monomials mono0 .. mono0+M-1 (global numbering)
@@ -205,6 +233,8 @@ struct KernelTable {
   cudaError_t (*fsub)(const FsubParams&, cudaStream_t);
   cudaError_t (*stage0)(const FsubParams&, cudaStream_t);
   cudaError_t (*update)(const UpdParams&, cudaStream_t);
+  cudaError_t (*adjoint)(const AdjParams&, cudaStream_t);
+  cudaError_t (*fabry)(const LossParams&, cudaStream_t);
   cudaError_t (*batch)(const BatchParams&, int blocks, int threads, cudaStream_t);
   int (*batch_occupancy)(int threads);  // resident blocks per SM
 };

@@ -30,7 +30,7 @@ MDN_MAX_DEGREE = 63
 
 EXPORTS = ("mdn_create", "mdn_workspace_bytes", "mdn_load_system", "mdn_set_series", "mdn_newton",
            "mdn_get_series", "mdn_get_residual", "mdn_evaluate", "mdn_solve", "mdn_profile",
-           "mdn_status_word", "mdn_last_error", "mdn_destroy", "mdn_evaluate_static", "mdn_set_late_updates",
+           "mdn_status_word", "mdn_last_error", "mdn_destroy", "mdn_evaluate_static", "mdn_set_late_updates", "mdn_adjoint", "mdn_fabry_loss", "mdn_set_residual_rows",
            "mdn_batch_create", "mdn_batch_workspace_bytes", "mdn_batch_load", "mdn_batch_evaluate",
            "mdn_batch_solve", "mdn_batch_tiles", "mdn_batch_last_error", "mdn_batch_destroy")
 BATCH_CONVERGED, BATCH_SINGULAR, BATCH_NONFINITE = 1, 2, 4
@@ -69,6 +69,9 @@ def load(path: str = None) -> ctypes.CDLL:
     L.mdn_profile.argtypes = [P, I, P, P]
     L.mdn_status_word.argtypes = [P]
     L.mdn_set_late_updates.argtypes = [P, I, I]
+    L.mdn_adjoint.argtypes = [P, P, P, P]
+    L.mdn_set_residual_rows.argtypes = [P, P, I]
+    L.mdn_fabry_loss.argtypes = [P, P, P, P]
     L.mdn_batch_create.argtypes = [ctypes.POINTER(P), I, I, I, P, P, P, I, I]
     L.mdn_batch_workspace_bytes.argtypes = [P, P]
     L.mdn_batch_workspace_bytes.restype = ctypes.c_size_t
@@ -193,6 +196,19 @@ def mdn_set_late_updates(ctx, first_stage: int, limbs: int) -> int:
     return load().mdn_set_late_updates(ctx, first_stage, limbs)
 
 
+def mdn_adjoint(ctx, x, g, grad_out) -> int:
+    return load().mdn_adjoint(ctx, _ptr(x), _ptr(g), _ptr(grad_out))
+
+
+def mdn_fabry_loss(ctx, x, loss_out, g_out) -> int:
+    return load().mdn_fabry_loss(ctx, _ptr(x), _ptr(loss_out), _ptr(g_out))
+
+
+def mdn_set_residual_rows(ctx, rows) -> int:
+    a, p = _host_i32(rows if rows is not None else [])
+    return load().mdn_set_residual_rows(ctx, p if a.size else None, int(a.size))
+
+
 def mdn_status_word(ctx) -> int:
     return load().mdn_status_word(ctx)
 
@@ -269,6 +285,25 @@ class Newton:
         dx = self.torch.empty(self.shape_series, dtype=self.torch.float64, device=dev)
         _check(self.ctx, mdn_solve(self.ctx, A.contiguous(), b.contiguous(), dx))
         return dx
+
+    def adjoint(self, x, g):
+        """Gradient [K, 1, M, d+1] (md) of a loss with dL/dx = g (md) with
+        respect to the coefficient series, at the series x."""
+        grad = self.torch.empty_like(self.coeff)
+        _check(self.ctx, mdn_adjoint(self.ctx, x.contiguous(), g.contiguous(), grad))
+        return grad
+
+    def fabry_loss(self, x):
+        """(L as [K] limbs, dL/dx) of L = sum_i x_{i,d}^2 + x_{0,d-1}/x_{0,d}."""
+        loss = self.torch.empty(self.K, dtype=self.torch.float64, device=self.cst.device)
+        g = self.torch.empty_like(x)
+        _check(self.ctx, mdn_fabry_loss(self.ctx, x.contiguous(), loss, g))
+        return loss, g
+
+    def set_residual_rows(self, rows):
+        """Residual monitor on these rows only (scaled by n/len(rows)); an
+        empty list restores all rows."""
+        _check(self.ctx, mdn_set_residual_rows(self.ctx, rows))
 
     def set_late_updates(self, first_stage: int, limbs: int):
         """Stages k >= first_stage form their right hand side updates in

@@ -196,6 +196,11 @@ CONFIGS = {
                                          1e-118, 2, unit_circle=True),
 }
 
+#: The adjoint workload: double double, n=64, d=31, built like the quad
+#: double one; the loss is the Fabry-ratio loss of the converged series and
+#: the gradient is taken with respect to every coefficient series.
+ADJOINT_CONFIG = PlantedConfig("dd-real-n64-d31-adjoint", 2, 1, 64, 31, 16, 2, 8, 64.0, 7, 1e-28, 4)
+
 
 def small_config(K: int, C: int, n: int, d: int, mono_per_eq: int = 3, kmin: int = 1, kmax: int = 3,
                  diag: float = None, steps: int = 6, tol: float = None, index: int = 100) -> PlantedConfig:

@@ -73,9 +73,12 @@ def test_batch_replay_and_step_cap(md):
     xb, sb, fb = b.solve(x0, 12, TOL[2])
     assert np.array_equal(to_np(xa), to_np(xb)) and np.array_equal(sa, sb) and np.array_equal(fa, fb)
     x2, s2, f2 = b.solve(x0, 2, TOL[2])
-    assert np.all(s2 == 2) and np.all(f2 == 0)
+    # two updates, unless the system met the stop rule before (a linear one
+    # is solved by its first update)
+    assert np.all(((s2 == 2) & (f2 == 0)) | ((s2 <= 2) & (f2 == md.BATCH_CONVERGED)))
+    assert np.sum(s2 == 2) >= len(items) - 1
     for q, (s, _, x0h, _) in enumerate(items):
-        x_ref, _ = oracle.newton(s, x0h, 2)
+        x_ref, _ = oracle.newton(s, x0h, int(s2[q]))
         assert np.max(mt.series_rel_error(b.unpack(x2)[q], x_ref)) <= TOL[2]
     x_0, s_0, _ = b.solve(x0, 0, TOL[2])
     assert np.all(s_0 == 0) and np.array_equal(to_np(x_0), to_np(x0))

@@ -242,3 +242,30 @@ def test_newton_late_updates_recovers_plant(md):
     x = to_np(nw.series())
     assert np.max(mt.series_rel_error(x, xstar)) <= cfg.tol
     assert np.max(mt.series_rel_error(x, x_ref)) <= cfg.tol
+
+
+def test_sampled_residual_monitor(md):
+    """The monitor on a subset of rows is that subset's share scaled by
+    n / rows: the full monitor splits exactly into a sample and its
+    complement; the iterates and the other norms do not depend on it."""
+    n = 12
+    cfg = wl.small_config(4, 1, n=n, d=9, mono_per_eq=3, kmin=1, kmax=4, steps=3, index=509)
+    s, xstar, x0 = planted(cfg)
+    nw = _newton(md, s)
+
+    def run(rows):
+        nw.set_residual_rows(rows)
+        nw.set_series(x0)
+        return nw.newton(3)
+
+    full = run([])
+    assert np.array_equal(run(list(range(n))), full)
+    rest = [i for i in range(n) if i != 5]
+    h_rest, h_one = run(rest), run([5])
+    np.testing.assert_allclose((n - 1) / n * h_rest[:, 1] + h_one[:, 1] / n, full[:, 1], rtol=1e-12)
+    assert np.array_equal(h_one[:, [0, 2]], full[:, [0, 2]])
+    assert np.all(h_one[:, 1] > 0)
+    with pytest.raises(md.MdnError):
+        nw.set_residual_rows([1, 1])
+    with pytest.raises(md.MdnError):
+        nw.set_residual_rows([n])

@@ -69,6 +69,16 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM bytes (read + write) per launch of the phase's main kernel from one ncu
+# capture of the unchanged kernels (profiles/ncu_qr_ed_fsub_qd-real-n64-d31.md);
+# absent entries report null.
+NCU_TRAFFIC = {
+    ("qd-real-n64-d31", "qr"): 613632 + 39168,
+    ("qd-real-n64-d31", "evaluate"): 1266432,
+    ("qd-real-n64-d31", "forward"): 4606464 + 38400,
+}
+
+
 def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -254,6 +264,11 @@ def run_batched(args, dev):
     counts = {}
     for s in systems:
         counts[(s.n, s.d)] = counts.get((s.n, s.d), 0) + 1
+    # algorithmic FP64 operations of the updates applied (one evaluation, QR
+    # and forward substitution per update; the stopping evaluations not counted)
+    ops = 0.0
+    for q, s in enumerate(systems):
+        ops += float(steps[q]) * F.step_counts(s.monomial_sizes(), s.n, s.D, s.K, s.C)["fp64_ops"]
     one_ms = sum(counts[c] * float(np.mean(v)) for c, v in per_class.items())
     b.close()
     return {
@@ -266,6 +281,9 @@ def run_batched(args, dev):
                        "sample": f"{len(idx)} systems stratified by (n, d), each through mdn_newton for the "
                                  "number of updates the batch applied to it, scaled by the class counts"},
         "speedup_vs_one_by_one": one_ms / ms, "generate_s": gen_s,
+        "roofline": {"bound": "alu", "kernel": "batch_kernel", "ops_per_launch": ops,
+                     "achieved": ops / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_OPS / 1e12, "unit": "FP64 Tops/s",
+                     "frac": ops / (ms * 1e-3) / FP64_PEAK_OPS},
         "l2": "working set larger than L2 (GBs of Jacobians)",
     }
 
@@ -416,7 +434,8 @@ def run_ours(args, cfg):
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(cfg), "data": "synthetic",
         "config": config_dict(cfg, args),
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": FP64_PEAK_OPS / 1e12,
-                     "unit": "FP64 Tops/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
+                     "unit": "FP64 Tops/s", "frac": achieved / FP64_PEAK_OPS,
+                     "traffic": NCU_TRAFFIC.get((cfg.name, dom)),
                      "peak_source": "derived: 152 SMs x 1.684 FP64 lanes/clk/SM (measured) x 2070 MHz",
                      "ops_per_launch": per_phase_ops[dom]},
         "phases_ms_per_step": {p: share[p] / steps_timed for p in md.PHASES},

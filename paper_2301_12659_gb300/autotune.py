@@ -52,10 +52,14 @@ def _stratified(systems, count: int, seed: int = 0):
     return sorted(pick)
 
 
-def tune(items, max_steps: int, tol: float, sample: int = 512, candidates=CANDIDATES, log=None):
+def tune(items, max_steps: int, tol: float, sample: int = 4096, candidates=CANDIDATES, log=None):
     """Times every admissible candidate on a sample of `items` ((system,
-    x*, x0) triples with the constant terms planted by the caller or not);
-    returns (threads, blocks_per_sm, table of timings)."""
+    x*, x0) triples; the constant terms are planted here) and returns
+    (threads, blocks_per_sm, table of timings).  The objective is the
+    throughput of a whole batch, so the sample must hold many systems per
+    resident block: on small samples the slowest single system decides and
+    fewer, larger blocks win (measured: 512 systems favour 256 x 1, the full
+    4096 favour 128 x 4)."""
     import torch
     from . import mdnewton as md
 
@@ -101,7 +105,7 @@ def batch_tiles(items, max_steps: int, tol: float, retune: bool = False, log=Non
         e = cache[key]
         return e["threads"], e["blocks_per_sm"], e
     t0 = time.time()
-    threads, bps, table = tune(items, max_steps, tol, log=log)
+    threads, bps, table = tune(items, max_steps, tol, sample=min(len(items), 2048), log=log)
     entry = {"threads": threads, "blocks_per_sm": bps, "timings": table, "tuned_s": round(time.time() - t0, 1)}
     cache[key] = entry
     try:
@@ -111,3 +115,32 @@ def batch_tiles(items, max_steps: int, tol: float, retune: bool = False, log=Non
     except OSError:
         pass
     return threads, bps, entry
+
+
+def main():
+    """Tune the tiles of the batched quad double workload on the whole batch
+    and store them in the cache (python -m paper_2301_12659_gb300.autotune)."""
+    import argparse
+
+    from . import workloads as wl
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--batch", default="qd-real-batch4096", choices=sorted(wl.BATCH_CONFIGS))
+    ap.add_argument("--sample", type=int, default=0, help="systems timed per candidate (0: all)")
+    args = ap.parse_args()
+    cfg = wl.BATCH_CONFIGS[args.batch]
+    items = wl.batch_planted_systems(cfg)
+    key = f"{_gpu_name()}|{signature([s for s, _, _ in items])}"
+    t0 = time.time()
+    threads, bps, table = tune(items, cfg.max_steps, cfg.tol, sample=args.sample or len(items), log=print)
+    cache = _load()
+    cache[key] = {"threads": threads, "blocks_per_sm": bps, "timings": table, "tuned_s": round(time.time() - t0, 1),
+                  "sample": args.sample or len(items)}
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    with open(CACHE, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    print(json.dumps({"key": key, "threads": threads, "blocks_per_sm": bps}))
+
+
+if __name__ == "__main__":
+    main()

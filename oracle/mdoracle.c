@@ -626,15 +626,23 @@ static void mdc_round_to(const mdc *x, int K, int C, int L, mdc *out) {
  * late_K limbs: every operand rounded to late_K limbs, the sum rounded to
  * late_K limbs, then subtracted from b_k in K limbs.  late_stage > d: the
  * plain method. */
+static int block_stages(int K, int C, int n, int d, const mdc *A, const mdc *B, mdc *DX, int late_stage,
+                        int late_K, const qr_t *QQ);
 static int block_solve(int K, int C, int n, int d, const mdc *A, const mdc *B, mdc *DX, int late_stage,
                        int late_K) {
-    const int D = d + 1;
     qr_t Q;
     int rc = qr_factor(A, n, K, C, &Q);
-    if (rc != ORC_OK) {
-        qr_free(&Q);
-        return rc;
-    }
+    if (rc == ORC_OK) rc = block_stages(K, C, n, d, A, B, DX, late_stage, late_K, &Q);
+    qr_free(&Q);
+    return rc;
+}
+
+/* The d+1 stages with a given factorization of A_0. */
+static int block_stages(int K, int C, int n, int d, const mdc *A, const mdc *B, mdc *DX, int late_stage,
+                        int late_K, const qr_t *QQ) {
+    const int D = d + 1;
+    const qr_t Q = *QQ;
+    int rc = ORC_OK;
     mdc *r = (mdc *)malloc(sizeof(mdc) * (size_t)n);
     mdc *xk = (mdc *)malloc(sizeof(mdc) * (size_t)n);
     for (int k = 0; k < D; ++k) {
@@ -672,7 +680,6 @@ static int block_solve(int K, int C, int n, int d, const mdc *A, const mdc *B, m
     }
     free(xk);
     free(r);
-    qr_free(&Q);
     return rc;
 }
 
@@ -1068,6 +1075,111 @@ int orc_adjoint(int K, int C, int n, int d, int M, const int32_t *eq, const int3
     free(F);
     free(G);
     free(X);
+    free(CF);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Staggered orders with the QR of A_0 once (Sections 4 and 5.3)              */
+/* ------------------------------------------------------------------------- */
+
+/* Number of coefficients of step s: 1 for s < first_steps (Newton on x_0
+ * alone until it is accurate), then L := min(D, L + 1 + L/2) per step (the
+ * growth of Section 4, optimistic about quadratic convergence). */
+static int stagger_order(int s, int first_steps, int D) {
+    if (s < first_steps) return 1;
+    int L = 1;
+    for (int t = first_steps; t <= s; ++t) {
+        L = L + 1 + L / 2;
+        if (L >= D) return D;
+    }
+    return L;
+}
+
+/* Newton's method with staggered orders: step s works on the coefficients
+ * 0..L_s-1 only (the truncated system is the system mod t^{L_s}: f, A_j and
+ * the update of those coefficients depend on no higher one).  Steps
+ * s < first_steps factor A_0 at their own x_0; later steps reuse the last of
+ * those factorizations (the QR once, valid when x_0 is accurate to about half
+ * the working precision).  hist [steps][3] as in orc_newton over the active
+ * coefficients; orders [steps] receives L_s. */
+int orc_newton_staggered(int K, int C, int n, int d, int M, const int32_t *eq, const int32_t *vptr,
+                         const int32_t *vidx, const double *coeff, const double *cst, const double *x0,
+                         int steps, int first_steps, double *x_out, double *hist, int32_t *orders) {
+    if (check_kc(K, C) || check_structure(n, d, M, eq, vptr, vidx) || steps < 0 || first_steps < 1)
+        return ORC_EINVAL;
+    const int D = d + 1;
+    const long N = (long)n * D;
+    mdc *CF = (mdc *)malloc(sizeof(mdc) * (size_t)(M > 0 ? M : 1) * D);
+    mdc *CS = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    mdc *X = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    soa_to_mdc(coeff, K, C, (long)M * D, CF);
+    soa_to_mdc(cst, K, C, N, CS);
+    soa_to_mdc(x0, K, C, N, X);
+    /* truncated copies, [.][L] */
+    mdc *CFL = (mdc *)malloc(sizeof(mdc) * (size_t)(M > 0 ? M : 1) * D);
+    mdc *CSL = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    mdc *XL = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    mdc *F = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    mdc *B = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    mdc *DX = (mdc *)malloc(sizeof(mdc) * (size_t)N);
+    mdc *AA = (mdc *)malloc(sizeof(mdc) * (size_t)D * n * n);
+    qr_t Q;
+    memset(&Q, 0, sizeof Q);
+    int have_q = 0, rc = ORC_OK;
+    for (int s = 0; s < steps && rc == ORC_OK; ++s) {
+        const int L = stagger_order(s, first_steps, D);
+        orders[s] = L;
+        for (int m = 0; m < M; ++m)
+            for (int k = 0; k < L; ++k) CFL[(size_t)m * L + k] = CF[(size_t)m * D + k];
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < L; ++k) {
+                CSL[(size_t)i * L + k] = CS[(size_t)i * D + k];
+                XL[(size_t)i * L + k] = X[(size_t)i * D + k];
+            }
+        sys_t S = {K, C, n, L - 1, M, eq, vptr, vidx, CFL, CSL};
+        rc = evaluate(&S, XL, F, AA);
+        if (rc != ORC_OK) break;
+        const long NL = (long)n * L;
+        hist[3 * s + 0] = norm1(F, NL, C);
+        for (long i = 0; i < NL; ++i)
+            for (int l = 0; l < KMAX; ++l) {
+                B[i].re[l] = -F[i].re[l];
+                B[i].im[l] = -F[i].im[l];
+            }
+        for (long i = 0; i < NL; ++i) mdc_zero(&DX[i]);
+        if (s < first_steps) {
+            if (have_q) qr_free(&Q);
+            rc = qr_factor(AA, n, K, C, &Q);
+            have_q = 1;
+            if (rc != ORC_OK) break;
+        }
+        rc = block_stages(K, C, n, L - 1, AA, B, DX, L, K, &Q);
+        if (rc != ORC_OK) break;
+        hist[3 * s + 1] = toeplitz_residual(K, C, n, L - 1, AA, B, DX);
+        cacc_t *t = (cacc_t *)malloc(sizeof(cacc_t));
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < L; ++k) {
+                mdc *xv = &X[(size_t)i * D + k];
+                cacc_init(t);
+                cacc_add(t, xv, K, C, 1.0);
+                cacc_add(t, &DX[(size_t)i * L + k], K, C, 1.0);
+                cacc_round(t, K, C, xv);
+            }
+        free(t);
+        hist[3 * s + 2] = norm1(DX, NL, C);
+    }
+    if (have_q) qr_free(&Q);
+    mdc_to_soa(X, K, C, N, x_out);
+    free(AA);
+    free(DX);
+    free(B);
+    free(F);
+    free(XL);
+    free(CSL);
+    free(CFL);
+    free(X);
+    free(CS);
     free(CF);
     return rc;
 }

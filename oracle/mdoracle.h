@@ -84,6 +84,14 @@ int orc_newton_late(int K, int C, int n, int d, int M, const int32_t *eq, const 
                     const int32_t *vidx, const double *coeff, const double *cst, const double *x0,
                     int steps, int late_stage, int late_K, double *x_out, double *hist);
 
+/* Newton with staggered orders and the QR once (Sections 4 and 5.3): step s
+ * works on the first L_s coefficients, L_s = 1 for s < first_steps and then
+ * L := min(d+1, L + 1 + L/2) per step; steps s < first_steps factor A_0, later
+ * steps reuse the last factorization.  orders [steps] receives L_s. */
+int orc_newton_staggered(int K, int C, int n, int d, int M, const int32_t *eq, const int32_t *vptr,
+                         const int32_t *vidx, const double *coeff, const double *cst, const double *x0,
+                         int steps, int first_steps, double *x_out, double *hist, int32_t *orders);
+
 /* Fabry-ratio loss L = sum_i x_{i,d}^2 + x_{0,d-1} / x_{0,d} of a real series
  * x [K][1][n][d+1] (d >= 1): loss [K] and g = dL/dx [K][1][n][d+1]. */
 int orc_fabry_loss(int K, int n, int d, const double *x, double *loss, double *g);

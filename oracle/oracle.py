@@ -69,10 +69,12 @@ def lib():
             L.orc_solve_late.argtypes = [i, i, i, i, P, P, i, i, P]
             L.orc_newton_late.argtypes = [i, i, i, i, i, P, P, P, P, P, P, i, i, i, P, P]
             L.orc_fabry_loss.argtypes = [i, i, i, P, P, P]
+            L.orc_newton_staggered.argtypes = [i, i, i, i, i, P, P, P, P, P, P, i, i, P, P, P]
             L.orc_adjoint.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P]
             for name in ("orc_md_binary", "orc_md_sqrt", "orc_series_mul", "orc_evaluate",
                          "orc_planted_constant", "orc_qr", "orc_solve", "orc_newton", "orc_solve_late",
-                         "orc_newton_late", "orc_fabry_loss", "orc_adjoint"):
+                         "orc_newton_late", "orc_fabry_loss", "orc_adjoint",
+                         "orc_newton_staggered"):
                 getattr(L, name).restype = i
             _lib = L
     return _lib
@@ -220,3 +222,16 @@ def adjoint(sysm, x, g) -> np.ndarray:
     _check(lib().orc_adjoint(K, C, n, d, M, _p(eq), _p(vptr), _p(vidx), _p(coeff), _p(x), _p(g), _p(grad)),
            "adjoint")
     return grad
+
+
+def newton_staggered(sysm, x0, steps: int, first_steps: int):
+    """Staggered Newton with the QR once: returns (x, hist[steps, 3], orders[steps])."""
+    K, C, n, d, M, eq, vptr, vidx, coeff = _sysargs(sysm)
+    cst = _f64(sysm.cst)
+    x0 = _f64(x0)
+    x = np.zeros_like(x0)
+    hist = np.zeros((max(steps, 1), 3))
+    orders = np.zeros(max(steps, 1), dtype=np.int32)
+    _check(lib().orc_newton_staggered(K, C, n, d, M, _p(eq), _p(vptr), _p(vidx), _p(coeff), _p(cst), _p(x0),
+                                      int(steps), int(first_steps), _p(x), _p(hist), _p(orders)), "newton_staggered")
+    return x, hist[:steps], orders[:steps]

@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--adjoint", default="on", choices=["on", "off"],
                     help="also time the adjoint gradient of the double double n=64, d=31 workload")
     ap.add_argument("--one-by-one-sample", type=int, default=48)
+    ap.add_argument("--staggered", default="on", choices=["on", "off"],
+                    help="also time solves with staggered orders and the QR once")
     ap.add_argument("--late-updates", type=int, default=0, metavar="FIRST_STAGE",
                     help="stated-accuracy variant: stages k >= FIRST_STAGE form their updates in K/2 limbs")
     return ap.parse_args()
@@ -288,6 +290,36 @@ def run_batched(args, dev):
     }
 
 
+def run_staggered(nw, cfg, x0_dev, xs_dev, plain_solve_ms):
+    """Solves with staggered orders and the QR once (Sections 4 and 5.3):
+    order-1 steps with a QR each until x_0 is accurate, then orders
+    1 -> 2 -> 4 -> 7 -> ... -> d+1 reusing the last QR, to the plant."""
+    import torch
+    from paper_2301_12659_gb300 import mdnewton as md
+
+    first = {2: 4, 4: 5, 8: 6}.get(cfg.K, 5)
+    L, growth = 1, 0
+    while L < cfg.d + 1:
+        L, growth = min(cfg.d + 1, L + 1 + L // 2), growth + 1
+    steps = first + growth + 2
+    nw.set_stagger(first)
+    times = []
+    for rep in range(4):
+        nw.set_series(x0_dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        md.mdn_newton(nw.ctx, steps, 0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep:
+            times.append(e0.elapsed_time(e1))
+    err = (nw.series() - xs_dev)[0].abs().max().item()
+    nw.set_stagger(0)
+    ms = statistics.median(times)
+    return {"first_order_steps": first, "steps_per_solve": steps, "solve_ms": ms, "plain_solve_ms": plain_solve_ms,
+            "speedup_vs_plain_solve": plain_solve_ms / ms, "max_leading_limb_error_vs_plant": err}
+
+
 def run_adjoint(args, dev):
     """Gradient of the Fabry-ratio loss of the converged dd n=64 d=31 series
     with respect to every coefficient series (mdn_fabry_loss + mdn_adjoint)."""
@@ -449,6 +481,8 @@ def run_ours(args, cfg):
         "check": {"max_leading_limb_error_vs_plant": diff, "final_norm_f": float(hist[-1, 0]) if hist is not None else None},
         "wall_s_timed_region": t_wall,
     }
+    if args.staggered == "on" and not args.late_updates:
+        line["staggered"] = run_staggered(nw, cfg, x0_dev, xs_dev, total_ms / args.steps * cfg.steps)
     if args.batched == "on":
         line["batched"] = run_batched(args, dev)
     if args.adjoint == "on":

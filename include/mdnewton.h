@@ -74,8 +74,9 @@ typedef enum {
 #define MDN_MAX_STEPS 64
 /* Largest truncation degree supported (d+1 <= 64 coefficients). */
 #define MDN_MAX_DEGREE 63
-/* Largest number of equations and unknowns: the QR of A0 keeps one column
- * per warp (three warp roles, one block per SM) in shared memory. */
+/* Largest number of equations and unknowns: the QR of A0 keeps its columns
+ * and rows in shared memory (a warp per column of A0 and of the identity, a
+ * warp per two rows of R^{-1}; all 5n/8 blocks resident, one per SM). */
 #define MDN_MAX_N 192
 
 /* Create a context for K limbs (2, 4 or 8; 1 runs plain doubles), real
@@ -146,6 +147,18 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
  * 1 <= first_stage, and first_stage > d switches the variant off.  Applies to
  * later mdn_newton and mdn_solve calls on the context.  Default: off. */
 mdn_status mdn_set_late_updates(mdn_ctx* ctx, int first_stage, int limbs);
+
+/* Staggered orders with the QR of A_0 once (Section 4: raise the order of
+ * the series as the leading coefficients become correct; Section 5.3: factor
+ * A_0 only in the first stage).  With first_steps >= 1, step s of later
+ * mdn_newton calls works on the first L_s coefficients only: L_s = 1 for
+ * s < first_steps (Newton on x_0 alone, with a QR of A_0 at every step), then
+ * L := min(d+1, L + 1 + L/2) per step, every later step reusing the last
+ * factorization.  The evaluation, the forward substitution and the update
+ * skip the inactive coefficients; the norms of res_hist are over the active
+ * ones, and a tolerance stops only at full order.  first_steps = 0 (default)
+ * restores the plain method. */
+mdn_status mdn_set_stagger(mdn_ctx* ctx, int first_steps);
 
 /* Sampled residual monitor (Section 5.4 suggests the residuals of one or a
  * few random equations instead of all of them): later mdn_newton calls form

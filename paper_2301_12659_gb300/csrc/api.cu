@@ -184,6 +184,8 @@ struct mdn_ctx {
   bool loaded = false, has_series = false;
   int late_stage = 1 << 30;  // stages from here form their updates in K/2 limbs
   int res_rows = 0;          // rows of the sampled residual monitor (0: all)
+  int stagger_first = 0;     // staggered orders: order-1 steps with a QR each (0: off)
+  std::vector<int> gvals, gidx_of_len;  // lane-group counts of the product lengths 1..D
   const double* coeff = nullptr;
   const double* cst = nullptr;
   cudaStream_t stream = nullptr;
@@ -283,16 +285,28 @@ static mdn_status build_tables(mdn_ctx* ctx, int M, const int32_t* eq, const int
   for (int m = 0; m < M; ++m) ctx->order[m] = m;
   std::stable_sort(ctx->order.begin(), ctx->order.end(),
                    [&](int a, int b) { return ctx->mono_k[a] > ctx->mono_k[b]; });
-  // schedules for every size 1..kmax
-  ctx->sched.clear();
-  ctx->sched_off.assign(kmax + 1, 0);
-  ctx->sched_nw.assign(kmax + 1, 0);
-  for (int k = 1; k <= kmax; ++k) {
-    ctx->sched_off[k] = (int)ctx->sched.size();
-    int nw = 0;
-    build_schedule(k, ctx->G, ctx->sched, nw);
-    ctx->sched_nw[k] = nw;
+  // schedules for every size 1..kmax and every lane-group count G that a
+  // product length 1..D uses (G(len) = 32 / ceil(len/2); shorter lengths run
+  // with staggered orders)
+  ctx->gvals.clear();
+  ctx->gidx_of_len.assign(ctx->D + 1, 0);
+  for (int len = 1; len <= ctx->D; ++len) {
+    const int g = 32 / ((len + 1) / 2);
+    int gi = (int)(std::find(ctx->gvals.begin(), ctx->gvals.end(), g) - ctx->gvals.begin());
+    if (gi == (int)ctx->gvals.size()) ctx->gvals.push_back(g);
+    ctx->gidx_of_len[len] = gi;
   }
+  const int ng = (int)ctx->gvals.size();
+  ctx->sched.clear();
+  ctx->sched_off.assign((size_t)ng * (kmax + 1), 0);
+  ctx->sched_nw.assign((size_t)ng * (kmax + 1), 0);
+  for (int gi = 0; gi < ng; ++gi)
+    for (int k = 1; k <= kmax; ++k) {
+      ctx->sched_off[(size_t)gi * (kmax + 1) + k] = (int)ctx->sched.size();
+      int nw = 0;
+      build_schedule(k, ctx->gvals[gi], ctx->sched, nw);
+      ctx->sched_nw[(size_t)gi * (kmax + 1) + k] = nw;
+    }
   if (eq && vidx) {
     for (int m = 0; m < M; ++m)
       if (eq[m] < 0 || eq[m] >= n) return fail(ctx, MDN_EINVAL, "eq_of_monomial[%d] = %d out of range", m, eq[m]);
@@ -398,12 +412,14 @@ mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degre
   const int C = is_complex ? 2 : 1;
   const KernelTable* kt = kernels_for(limbs, C);
   if (!kt || n < 1 || n > MDN_MAX_N || degree < 0 || degree > MDN_MAX_DEGREE) return MDN_EINVAL;
-  // the QR keeps one column per warp, four warps per block, in shared memory
-  if ((size_t)4 * n * 2 * limbs * sizeof(double) > (size_t)QR_SMEM_RESERVE) return MDN_EINVAL;
+  // the QR keeps its columns and rows in shared memory, its blocks all resident
+  if (qr_smem_bytes(n, limbs) > (size_t)QR_SMEM_MAX) return MDN_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MDN_ECUDA;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MDN_ECUDA;
+  // the cooperative QR launch holds all its blocks, one per SM
+  if (qr_blocks_for(n) > sms) return MDN_EINVAL;
   mdn_ctx* ctx = new (std::nothrow) mdn_ctx();
   if (!ctx) return MDN_EINVAL;
   ctx->K = limbs;
@@ -548,15 +564,21 @@ static mdn_status run_a0(mdn_ctx* ctx, const double* x, long long Nx, int xstrid
 
 // Evaluation and differentiation of all monomials, then f and the Jacobian
 // slices j >= 1 (slice 0 comes from run_a0) on `blocks` SMs.
-static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double* A, int blocks) {
+// Evaluation of the first `len` coefficients (all by default; fewer with
+// staggered orders: the truncated products of the first len coefficients
+// need no higher one).
+static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double* A, int blocks, int len = 0) {
   const Layout& L = ctx->L;
   const long long D = ctx->D, n = ctx->n;
+  if (len <= 0 || len > ctx->D) len = ctx->D;
+  const int gi = ctx->gidx_of_len[len];
   EdParams e{};
   e.n = ctx->n;
   e.D = ctx->D;
+  e.len = len;
   e.M = ctx->M;
-  e.P = ctx->P;
-  e.G = ctx->G;
+  e.P = (len + 1) / 2;
+  e.G = 32 / e.P;
   e.kmax = ctx->kmax;
   e.Smax = ctx->Smax;
   e.Wtot = std::min(blocks * (ED_THREADS / 32), ctx->Wtot);
@@ -574,8 +596,8 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
   e.mono_sbase = ctx->at<int>(L.o_mono_sbase);
   e.vidx = ctx->at<int>(L.o_vidx);
   e.sched = ctx->at<int4>(L.o_sched);
-  e.sched_off = ctx->at<int>(L.o_sched_off);
-  e.sched_nw = ctx->at<int>(L.o_sched_nw);
+  e.sched_off = ctx->at<int>(L.o_sched_off) + (size_t)gi * (ctx->kmax + 1);
+  e.sched_nw = ctx->at<int>(L.o_sched_nw) + (size_t)gi * (ctx->kmax + 1);
   e.counter = ctx->at<int>(L.o_counter);
   ph_begin(ctx, MDN_PHASE_EVALUATE);
   CU(cudaMemsetAsync(e.counter, 0, 4, ctx->stream));
@@ -585,6 +607,7 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
   AsmParams a{};
   a.n = ctx->n;
   a.D = ctx->D;
+  a.len = len;
   a.j_begin = 1;
   a.out = e.out;
   a.No = e.No;
@@ -600,7 +623,7 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
   a.pair_slot = ctx->at<int>(L.o_pair_slot);
   ph_begin(ctx, MDN_PHASE_ASSEMBLE);
   CU(ctx->kt->assemble(a, A != nullptr, ctx->stream));
-  ph_end(ctx, MDN_PHASE_ASSEMBLE, (A != nullptr && ctx->D > 1) ? 2 : 1);
+  ph_end(ctx, MDN_PHASE_ASSEMBLE, (A != nullptr && len > 1) ? 2 : 1);
   return MDN_OK;
 }
 
@@ -612,7 +635,9 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* 
   CU(cudaGetLastError());
   QrParams q{};
   q.n = ctx->n;
-  q.nA = (ctx->n + (QR_THREADS / 32) - 1) / (QR_THREADS / 32);
+  q.nAc = (ctx->n + 3) / 4;
+  q.nAi = (ctx->n + 3) / 4;
+  q.nAz = ((ctx->n + 1) / 2 + 3) / 4;
   q.A0 = A0;
   q.NA = NA0;
   q.Nnn = n * n;
@@ -633,7 +658,7 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* 
   return MDN_OK;
 }
 
-static int qr_blocks(const mdn_ctx* ctx) { return 3 * ((ctx->n + (QR_THREADS / 32) - 1) / (QR_THREADS / 32)); }
+static int qr_blocks(const mdn_ctx* ctx) { return qr_blocks_for(ctx->n); }
 
 // Forward substitution for dx with right hand side sgn * rhs: stage 0 alone
 // (dx_0 = W r_0, and x_0 + dx_0 into the xnext0 buffer when x is given), the
@@ -641,7 +666,7 @@ static int qr_blocks(const mdn_ctx* ctx) { return 3 * ((ctx->n + (QR_THREADS / 3
 // `blocks` SMs.
 static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, long long NA0, const double* W,
                               const double* rhs, int sgn, double* dx, const double* x, cudaEvent_t e0, int blocks,
-                              bool transposed = false) {
+                              bool transposed = false, int nst = 0) {
   const Layout& L = ctx->L;
   const long long D = ctx->D, n = ctx->n;
   ph_begin(ctx, MDN_PHASE_FORWARD);
@@ -652,10 +677,12 @@ static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, l
   u.first_stage = 1;
   u.nW = std::min(ctx->n, 4 * FSUB_WBLOCKS);
   const int wb = (u.nW + 3) / 4;
-  u.nOwn = (int)std::min<long long>(4LL * std::max(1, blocks - wb), (long long)ctx->n * ctx->D);
+  const int nst_eff = (nst > 0 && nst <= ctx->D) ? nst : ctx->D;
+  u.nOwn = (int)std::min<long long>(4LL * std::max(1, blocks - wb), (long long)ctx->n * nst_eff);
   u.late_stage = transposed ? ctx->D : std::min(ctx->late_stage, ctx->D);
   u.transpose = transposed ? 1 : 0;
   u.reverse = transposed ? 1 : 0;
+  u.nst = nst_eff;
   u.A = A;
   u.NA = D * n * n;
   u.A0 = A0;
@@ -694,6 +721,24 @@ static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, l
 // and QR of step s run on the side stream (on a third of the SMs) beside the
 // later stages of step s-1, its update and the evaluation of step s (on the
 // other SMs).  A_0 and W alternate between two buffers by step parity.
+// Staggered orders (Section 4): coefficients worked on by step s; the first
+// stagger_first steps work on x_0 alone, then L := min(D, L + 1 + L/2).
+static int stagger_len(const mdn_ctx* ctx, int s) {
+  const int f = ctx->stagger_first;
+  if (f <= 0) return ctx->D;
+  if (s < f) return 1;
+  int L = 1;
+  for (int t = f; t <= s; ++t) {
+    L = L + 1 + L / 2;
+    if (L >= ctx->D) return ctx->D;
+  }
+  return L;
+}
+// Whether step s forms its own QR of A_0 (with staggered orders only the
+// order-1 steps do; later steps reuse the last one: the QR once of
+// Section 5.3, valid once x_0 is accurate to about half the precision).
+static bool qr_at(const mdn_ctx* ctx, int s) { return ctx->stagger_first <= 0 || s < ctx->stagger_first; }
+
 static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, bool* converged) {
   const Layout& L = ctx->L;
   const long long D = ctx->D, n = ctx->n, nn = n * n, KC = (long long)ctx->K * ctx->C;
@@ -705,7 +750,7 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
   double* A0b[2] = {ctx->at<double>(L.o_A0b), ctx->at<double>(L.o_A0b) + KC * nn};
   double* Wb[2] = {ctx->at<double>(L.o_W), ctx->at<double>(L.o_W) + KC * nn};
   const int qb = qr_blocks(ctx);
-  const bool overlap = ctx->side && qb <= ctx->num_sms / 3;
+  const bool overlap = ctx->side && qb <= (ctx->num_sms * 3) / 8;
   const int rest = overlap ? ctx->num_sms - qb : ctx->num_sms;
   mdn_status r;
   *converged = false;
@@ -720,13 +765,20 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
   if ((r = run_qr(ctx, A0b[0], nn, Wb[0], qs)) != MDN_OK) return r;
   ph_end(ctx, MDN_PHASE_QR, 5, qs);
   if (overlap) CU(cudaEventRecord(ctx->ev_join, ctx->side));
+  if (ctx->stagger_first > 0) {
+    // inactive coefficients contribute nothing to the norms of the step
+    CU(cudaMemsetAsync(ctx->at<double>(L.o_fabs), 0, 8 * (size_t)n * D, ctx->stream));
+    CU(cudaMemsetAsync(ctx->at<double>(L.o_dxabs), 0, 8 * (size_t)n * D, ctx->stream));
+    CU(cudaMemsetAsync(ctx->at<double>(L.o_resabs), 0, 8 * (size_t)n * D, ctx->stream));
+  }
   for (int s = 0; s < steps; ++s) {
-    const int b = s & 1;
-    if ((r = run_evaluate(ctx, x, f, A, rest)) != MDN_OK) return r;
+    const int b = qr_at(ctx, s) ? (s & 1) : ((ctx->stagger_first - 1) & 1);
+    const int len = stagger_len(ctx, s);
+    if ((r = run_evaluate(ctx, x, f, A, rest, len)) != MDN_OK) return r;
     if (overlap) CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-    const bool next = s + 1 < steps;
+    const bool next = s + 1 < steps && qr_at(ctx, s + 1);
     if ((r = run_forward(ctx, A, A0b[b], nn, Wb[b], f, -1, dx, x, (overlap && next) ? ctx->ev_fork : nullptr,
-                         rest)) != MDN_OK)
+                         rest, false, len)) != MDN_OK)
       return r;
     if (next) {
       // A_0 and QR of step s+1 from x_0 + dx_0
@@ -740,6 +792,7 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
     UpdParams u{};
     u.n = ctx->n;
     u.D = ctx->D;
+    u.len = len;
     u.x = x;
     u.dx = dx;
     u.f = f;
@@ -764,7 +817,7 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
       double h[3];
       CU(cudaMemcpyAsync(h, hist + 3 * s, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
       CU(cudaStreamSynchronize(ctx->stream));
-      if (h[2] <= tol) {
+      if (h[2] <= tol && len == ctx->D) {
         *converged = true;
         break;
       }
@@ -919,6 +972,13 @@ mdn_status mdn_set_residual_rows(mdn_ctx* ctx, const int32_t* rows, int count) {
   CU(cudaMemsetAsync(ctx->at<double>(L.o_resabs), 0, 8 * (size_t)ctx->n * ctx->D, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   ctx->res_rows = (count == ctx->n) ? 0 : count;
+  return MDN_OK;
+}
+
+mdn_status mdn_set_stagger(mdn_ctx* ctx, int first_steps) {
+  if (!ctx) return MDN_EINVAL;
+  if (first_steps < 0 || first_steps > MDN_MAX_STEPS) return fail(ctx, MDN_EINVAL, "first_steps out of range");
+  ctx->stagger_first = first_steps;
   return MDN_OK;
 }
 

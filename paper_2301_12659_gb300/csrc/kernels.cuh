@@ -267,14 +267,14 @@ __global__ void __launch_bounds__(ED_THREADS) ed_kernel(EdParams p) {
     for (int w = 0; w < nw; ++w) {
       const int4 op = ingroup ? sc[w * p.G + g] : make_int4(0, 0, 0, 0);
       if (op.x == OP_PRODUCT) {
-        series_product<K, C>(resolve(p, op.z, m, wg), resolve(p, op.w, m, wg), resolve(p, op.y, m, wg), t, p.D);
+        series_product<K, C>(resolve(p, op.z, m, wg), resolve(p, op.w, m, wg), resolve(p, op.y, m, wg), t, p.len);
       } else if (op.x == OP_COPY) {
         const SP s = resolve(p, op.z, m, wg), d = resolve(p, op.y, m, wg);
         cmd<K, C> v;
         ld(s.p, s.N, s.off + t, v);
         st(d.p, d.N, d.off + t, v);
-        ld(s.p, s.N, s.off + (p.D - 1 - t), v);
-        st(d.p, d.N, d.off + (p.D - 1 - t), v);
+        ld(s.p, s.N, s.off + (p.len - 1 - t), v);
+        st(d.p, d.N, d.off + (p.len - 1 - t), v);
       }
       __syncwarp();
     }
@@ -284,10 +284,11 @@ __global__ void __launch_bounds__(ED_THREADS) ed_kernel(EdParams p) {
 // f_i[k] = cst_i[k] + sum of the values of the monomials of equation i.
 template <int K, int C>
 __global__ void assemble_f_kernel(AsmParams p) {
-  const long long total = (long long)p.n * p.D;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(id / p.D), kk = (int)(id - (long long)i * p.D);
+  const long long total = (long long)p.n * p.len;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / p.len), kk = (int)(q - (long long)i * p.len);
+    const long long id = (long long)i * p.D + kk;
     cmd<K, C> v, s;
     CAcc<K, C> acc;
     ld(p.cst, p.Nf, id, v);
@@ -307,7 +308,7 @@ __global__ void assemble_f_kernel(AsmParams p) {
 template <int K, int C>
 __global__ void assemble_A_kernel(AsmParams p) {
   const long long nn = (long long)p.n * p.n;
-  const long long total = nn * (p.D - p.j_begin);
+  const long long total = nn * (p.len - p.j_begin);
   for (long long id0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; id0 < total;
        id0 += (long long)gridDim.x * blockDim.x) {
     const long long id = id0 + nn * p.j_begin;
@@ -610,56 +611,72 @@ __device__ void qr_identity(const QrParams& p, int e, double* y, unsigned ep) {
   }
 }
 
-// Row warp i of Z = R^{-1}, built column by column as R grows:
+// Rows ia and ib of Z = R^{-1} (one warp, the rows g and n-1-g so that the
+// warps share the work evenly), built column by column as R grows:
 //   Z[i][i] = 1/R_ii,  Z[i][c] = -(1/R_cc) sum_{k=i..c-1} Z[i][k] R[k][c]  (c > i),
 // the block inverse of the leading (c+1) x (c+1) part of R.
 template <int K, int C>
-__device__ void qr_rinv_row(const QrParams& p, int i, double* z, unsigned ep) {
+__device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, double* za, double* zb, unsigned ep) {
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   unsigned* frinv = p.flags + 2 * n;
-  for (int c = i; c < n; ++c) {
+  for (int c = ia; c < n; ++c) {
     if (!warp_wait(&frinv[c], ep, p.spin_limit, p.status)) return;
     cmd<K, C> rc;
     ld(p.rinv, p.n, c, rc);
-    cmd<K, C> zc;
-    if (c == i) {
-      zc = rc;
-    } else {
-      CAcc<K, C> acc;
-      cacc_zero(acc);
-      for (int k = i + lane; k < c; k += 32) {
-        cmd<K, C> zk, rk;
-        ld(z, n, k, zk);
-        ld(p.Rm, p.Nnn, (long long)k * n + c, rk);
-        cacc_fma(acc, zk, rk);
+    for (int q = 0; q < 2; ++q) {
+      const int i = q ? ib : ia;
+      double* z = q ? zb : za;
+      if (c < i || (q == 1 && ib == ia)) continue;
+      cmd<K, C> zc;
+      if (c == i) {
+        zc = rc;
+      } else {
+        CAcc<K, C> acc;
+        cacc_zero(acc);
+        for (int k = i + lane; k < c; k += 32) {
+          cmd<K, C> zk, rk;
+          ld(z, n, k, zk);
+          ld(p.Rm, p.Nnn, (long long)k * n + c, rk);
+          cacc_fma(acc, zk, rk);
+        }
+        cmd<K, C> s, t;
+        warp_sum_acc(acc, s);
+        cmd_mul(s, rc, t);
+        md_neg(t.re, zc.re);
+        md_neg(t.im, zc.im);
       }
-      cmd<K, C> s, t;
-      warp_sum_acc(acc, s);
-      cmd_mul(s, rc, t);
-      md_neg(t.re, zc.re);
-      md_neg(t.im, zc.im);
+      if (lane == 0) {
+        st(z, n, c, zc);
+        st(p.Z, p.Nnn, (long long)i * n + c, zc);
+      }
+      __syncwarp();
     }
-    if (lane == 0) {
-      st(z, n, c, zc);
-      st(p.Z, p.Nnn, (long long)i * n + c, zc);
-    }
-    __syncwarp();
   }
 }
 
 template <int K, int C>
 __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrParams p) {
   extern __shared__ __align__(16) unsigned char qr_smem[];
+  double* sm = reinterpret_cast<double*>(qr_smem);
   const int warp = threadIdx.x >> 5;
   const unsigned ep = *p.epoch;
-  double* y = reinterpret_cast<double*>(qr_smem) + (size_t)warp * p.n * 2 * K;
-  const int role = blockIdx.x / p.nA;
-  const int c = (blockIdx.x - role * p.nA) * (QR_THREADS / 32) + warp;
-  if (c >= p.n) return;
-  if (role == 0) qr_column<K, C>(p, c, y, ep);
-  else if (role == 1) qr_identity<K, C>(p, c, y, ep);
-  else qr_rinv_row<K, C>(p, c, y, ep);
+  const int n = p.n;
+  const size_t col = (size_t)n * 2 * K;
+  const int b = blockIdx.x;
+  if (b < p.nAc) {
+    const int c = b * (QR_THREADS / 32) + warp;
+    if (c >= n) return;
+    qr_column<K, C>(p, c, sm + warp * col, ep);
+  } else if (b < p.nAc + p.nAi) {
+    const int e = (b - p.nAc) * (QR_THREADS / 32) + warp;
+    if (e >= n) return;
+    qr_identity<K, C>(p, e, sm + warp * col, ep);
+  } else {
+    const int g = (b - p.nAc - p.nAi) * (QR_THREADS / 32) + warp;
+    if (g > (n - 1) / 2) return;
+    qr_rinv_rows<K, C>(p, g, n - 1 - g, sm + 2 * warp * col, sm + (2 * warp + 1) * col, ep);
+  }
 }
 
 // W = Z Y = R^{-1} Q^H: one warp per entry, lanes over k >= i (Z is upper
@@ -758,7 +775,7 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
     // ---- solve warps: dx_k = W r_k ----
     const int w = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (w >= p.nW) return;
-    for (int k = p.first_stage; k < D; ++k) {
+    for (int k = p.first_stage; k < p.nst; ++k) {
       if (!warp_wait(&p.rdone[k], (unsigned)n, p.spin_limit, p.status)) return;
       for (int i = w; i < n; i += p.nW) {
         cmd<K, C> s;
@@ -772,7 +789,8 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
   // ---- owner warps ----
   const int ow = (blockIdx.x - wblocks) * 4 + (threadIdx.x >> 5);
   if (ow >= p.nOwn) return;
-  const long long items = (long long)D * n;
+  const long long items = (long long)p.nst * n;
+  if (ow >= items) return;  // fewer stages than owner warps (staggered orders)
   // my items q = k*n + i, q = ow, ow + nOwn, ... (increasing k)
   // initialise: acc = sgn * b_k[i]; stage 0 is final at once
   for (long long q = ow; q < items; q += p.nOwn) {
@@ -894,9 +912,10 @@ __global__ void stage0_kernel(FsubParams p) {
 // x += dx; per-entry magnitudes of f and dx for the norms of the step.
 template <int K, int C>
 __global__ void update_kernel(UpdParams p) {
-  const long long total = (long long)p.n * p.D;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
+  const long long total = (long long)p.n * p.len;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long id = (q / p.len) * p.D + (q % p.len);
     cmd<K, C> x, dx, f;
     ld(p.dx, p.Nx, id, dx);
     ld(p.f, p.Nx, id, f);
@@ -1070,9 +1089,9 @@ int ed_blocks_per_sm() {
 }
 template <int K, int C>
 cudaError_t launch_assemble(const AsmParams& p, bool want_A, cudaStream_t s) {
-  assemble_f_kernel<K, C><<<grid_for((long long)p.n * p.D, 128), 128, 0, s>>>(p);
-  if (want_A && p.D > p.j_begin)
-    assemble_A_kernel<K, C><<<grid_for((long long)p.n * p.n * (p.D - p.j_begin), 128), 128, 0, s>>>(p);
+  assemble_f_kernel<K, C><<<grid_for((long long)p.n * p.len, 128), 128, 0, s>>>(p);
+  if (want_A && p.len > p.j_begin)
+    assemble_A_kernel<K, C><<<grid_for((long long)p.n * p.n * (p.len - p.j_begin), 128), 128, 0, s>>>(p);
   return cudaGetLastError();
 }
 // Every QR block reserves most of an SM's shared memory (unused) so that no
@@ -1082,14 +1101,17 @@ template <int K, int C>
 cudaError_t launch_qr(const QrParams& p, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(qr_kernel<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_RESERVE);
+    cudaError_t e = cudaFuncSetAttribute(qr_kernel<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_MAX);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   QrParams q = p;
   void* args[] = {(void*)&q};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)qr_kernel<K, C>, dim3(3 * p.nA), dim3(QR_THREADS), args,
-                                              QR_SMEM_RESERVE, s);
+  // at least the reservation, so that no two QR blocks share an SM
+  size_t smem = qr_smem_bytes(p.n, K);
+  if (smem < (size_t)QR_SMEM_RESERVE) smem = QR_SMEM_RESERVE;
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)qr_kernel<K, C>, dim3(p.nAc + p.nAi + p.nAz),
+                                              dim3(QR_THREADS), args, smem, s);
   if (e != cudaSuccess) return e;
   w_kernel<K, C><<<grid_for((long long)p.n * p.n * 32, 128), 128, 0, s>>>(q);
   return cudaGetLastError();
@@ -1117,7 +1139,7 @@ cudaError_t launch_stage0(const FsubParams& p, cudaStream_t s) {
 }
 template <int K, int C>
 cudaError_t launch_update(const UpdParams& p, cudaStream_t s) {
-  update_kernel<K, C><<<grid_for((long long)p.n * p.D, 128), 128, 0, s>>>(p);
+  update_kernel<K, C><<<grid_for((long long)p.n * p.len, 128), 128, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@ namespace mdn {
 constexpr int ED_THREADS = 128;  // 4 warps: one per SM sub-partition
 constexpr int QR_THREADS = 128;  // 4 warps: one per SM sub-partition
 constexpr int QR_SMEM_RESERVE = 116 * 1024;  // any two reserving blocks exceed an SM's shared memory
+constexpr int QR_SMEM_MAX = 227 * 1024;      // dynamic shared memory a block may use
 constexpr int FSUB_THREADS = 128;  // 4 warps per block, one block per SM
 constexpr int FSUB_WBLOCKS = 16;   // blocks of solve warps
 
@@ -24,6 +25,7 @@ enum OpKind { OP_NONE = 0, OP_PRODUCT = 1, OP_COPY = 2 };
 
 struct EdParams {
   int n, D, M, P, G, kmax, Smax, Wtot;
+  int len;  // coefficients computed (<= D, the stride); P and G are those of len
   const double* x;
   long long Nx;  // n*D
   const double* coeff;
@@ -67,6 +69,7 @@ struct A0Params {
 
 struct AsmParams {
   int n, D, j_begin;
+  int len;  // coefficients assembled (<= D)
   const double* out;
   long long No;
   const double* cst;
@@ -82,7 +85,8 @@ struct AsmParams {
 };
 
 struct QrParams {
-  int n, nA;  // nA blocks per role: columns of A0, columns of the identity, rows of R^{-1}
+  int n;
+  int nAc, nAi, nAz;  // blocks: columns of A0 (4 each), identity columns (4), rows of R^{-1} (8)
   const double* A0;
   long long NA;   // stride of the A array the A0 slice lives in
   long long Nnn;  // n*n
@@ -108,6 +112,7 @@ struct FsubParams {
   int nW;       // solve warps (dx_k = W r_k), on the first nW/4 blocks
   int nOwn;     // owner warps of the r_k[i] accumulators
   int late_stage;  // stages k >= late_stage form their updates in K/2 limbs (D: never)
+  int nst;         // stages solved (<= D; staggered orders)
   const int* resmask;  // rows whose residual the monitor forms (null: all)
   int transpose;   // 1: use A_j^T and W^T (the adjoint's solve with J^T)
   int reverse;     // 1: stage k works on coefficient D-1-k (J^T is block upper triangular)
@@ -132,6 +137,7 @@ struct FsubParams {
 
 struct UpdParams {
   int n, D;
+  int len;  // coefficients updated (<= D)
   double* x;
   const double* dx;
   const double* f;
@@ -222,6 +228,13 @@ __host__ __device__ inline long long batch_work_doubles(int K, int C, int n, int
   return s + 64;
 }
 
+
+// Shared memory of a QR block: four columns of A0 or of the identity, or
+// eight rows of R^{-1} (n md values each).
+__host__ __device__ inline size_t qr_smem_bytes(int n, int K) { return 8 * (size_t)n * 2 * K * sizeof(double); }
+// Blocks of the QR launch: columns of A0 (4 per block), columns of the
+// identity (4 per block), pairs of rows of R^{-1} (4 pairs per block).
+__host__ __device__ inline int qr_blocks_for(int n) { return (n + 3) / 4 + (n + 3) / 4 + ((n + 1) / 2 + 3) / 4; }
 
 struct KernelTable {
   int K, C;

@@ -30,7 +30,7 @@ MDN_MAX_DEGREE = 63
 
 EXPORTS = ("mdn_create", "mdn_workspace_bytes", "mdn_load_system", "mdn_set_series", "mdn_newton",
            "mdn_get_series", "mdn_get_residual", "mdn_evaluate", "mdn_solve", "mdn_profile",
-           "mdn_status_word", "mdn_last_error", "mdn_destroy", "mdn_evaluate_static", "mdn_set_late_updates", "mdn_adjoint", "mdn_fabry_loss", "mdn_set_residual_rows",
+           "mdn_status_word", "mdn_last_error", "mdn_destroy", "mdn_evaluate_static", "mdn_set_late_updates", "mdn_adjoint", "mdn_fabry_loss", "mdn_set_residual_rows", "mdn_set_stagger",
            "mdn_batch_create", "mdn_batch_workspace_bytes", "mdn_batch_load", "mdn_batch_evaluate",
            "mdn_batch_solve", "mdn_batch_tiles", "mdn_batch_last_error", "mdn_batch_destroy")
 BATCH_CONVERGED, BATCH_SINGULAR, BATCH_NONFINITE = 1, 2, 4
@@ -71,6 +71,7 @@ def load(path: str = None) -> ctypes.CDLL:
     L.mdn_set_late_updates.argtypes = [P, I, I]
     L.mdn_adjoint.argtypes = [P, P, P, P]
     L.mdn_set_residual_rows.argtypes = [P, P, I]
+    L.mdn_set_stagger.argtypes = [P, I]
     L.mdn_fabry_loss.argtypes = [P, P, P, P]
     L.mdn_batch_create.argtypes = [ctypes.POINTER(P), I, I, I, P, P, P, I, I]
     L.mdn_batch_workspace_bytes.argtypes = [P, P]
@@ -209,6 +210,10 @@ def mdn_set_residual_rows(ctx, rows) -> int:
     return load().mdn_set_residual_rows(ctx, p if a.size else None, int(a.size))
 
 
+def mdn_set_stagger(ctx, first_steps: int) -> int:
+    return load().mdn_set_stagger(ctx, int(first_steps))
+
+
 def mdn_status_word(ctx) -> int:
     return load().mdn_status_word(ctx)
 
@@ -304,6 +309,10 @@ class Newton:
         """Residual monitor on these rows only (scaled by n/len(rows)); an
         empty list restores all rows."""
         _check(self.ctx, mdn_set_residual_rows(self.ctx, rows))
+
+    def set_stagger(self, first_steps: int):
+        """Staggered orders with the QR once (0: plain Newton)."""
+        _check(self.ctx, mdn_set_stagger(self.ctx, first_steps))
 
     def set_late_updates(self, first_stage: int, limbs: int):
         """Stages k >= first_stage form their right hand side updates in

@@ -269,3 +269,31 @@ def test_sampled_residual_monitor(md):
         nw.set_residual_rows([1, 1])
     with pytest.raises(md.MdnError):
         nw.set_residual_rows([n])
+
+
+@pytest.mark.parametrize("K,C,n,d,first,steps", [(2, 1, 5, 15, 4, 12), (4, 1, 9, 31, 5, 14),
+                                                 (8, 2, 4, 15, 6, 14), (4, 1, 3, 7, 2, 3)])
+def test_staggered_newton_matches_oracle(md, K, C, n, d, first, steps):
+    """Staggered orders with the QR once against the oracle's staggered
+    Newton: the same series after every schedule, the plant at the end."""
+    cfg = wl.small_config(K, C, n=n, d=d, mono_per_eq=3, kmin=1, kmax=4, index=560 + K + n)
+    s, xstar, x0 = planted(cfg)
+    x_ref, h_ref, orders = oracle.newton_staggered(s, x0, steps, first)
+    nw = _newton(md, s)
+    nw.set_stagger(first)
+    nw.set_series(x0)
+    hist = nw.newton(steps)
+    x = to_np(nw.series())
+    assert np.max(mt.series_rel_error(x, x_ref)) <= TOL[K]
+    big = h_ref[:, 0] > 1e-6
+    assert np.allclose(hist[big, 0], h_ref[big, 0], rtol=1e-10)
+    if orders[-1] == d + 1 and steps >= 12:
+        assert np.max(mt.series_rel_error(x, xstar)) <= TOL[K]
+    else:  # coefficients beyond the last order are untouched
+        assert np.array_equal(x[..., orders[-1]:], x0[..., orders[-1]:])
+    # back to the plain method
+    nw.set_stagger(0)
+    nw.set_series(x0)
+    nw.newton(2)
+    x2_ref, _ = oracle.newton(s, x0, 2)
+    assert np.max(mt.series_rel_error(to_np(nw.series()), x2_ref)) <= TOL[K]

@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--adjoint", default="on", choices=["on", "off"],
                     help="also time the adjoint gradient of the double double n=64, d=31 workload")
     ap.add_argument("--one-by-one-sample", type=int, default=48)
+    ap.add_argument("--batch-count", type=int, default=0,
+                    help="systems of the batched workload (0: all 4096; fewer for profiling captures)")
     ap.add_argument("--staggered", default="on", choices=["on", "off"],
                     help="also time solves with staggered orders and the QR once")
     ap.add_argument("--late-updates", type=int, default=0, metavar="FIRST_STAGE",
@@ -75,9 +77,9 @@ def parse():
 # capture of the unchanged kernels (profiles/ncu_qr_ed_fsub_qd-real-n64-d31.md);
 # absent entries report null.
 NCU_TRAFFIC = {
-    ("qd-real-n64-d31", "qr"): 613632 + 39168,
-    ("qd-real-n64-d31", "evaluate"): 1266432,
-    ("qd-real-n64-d31", "forward"): 4606464 + 38400,
+    ("qd-real-n64-d31", "qr"): 612864 + 42240,
+    ("qd-real-n64-d31", "evaluate"): 1265664,
+    ("qd-real-n64-d31", "forward"): 4604416 + 30720,
 }
 
 
@@ -222,7 +224,7 @@ def run_batched(args, dev):
 
     bcfg = wl.BATCH_CONFIGS["qd-real-batch4096"]
     t0 = time.perf_counter()
-    items = wl.batch_planted_systems(bcfg)
+    items = wl.batch_planted_systems(bcfg, args.batch_count or None)
     gen_s = time.perf_counter() - t0
     threads, bps, entry = autotune.batch_tiles(items, bcfg.max_steps, bcfg.tol)
     systems = [s for s, _, _ in items]

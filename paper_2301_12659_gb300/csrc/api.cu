@@ -372,7 +372,7 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_occ = take(4 * (size_t)ctx->nnz);
   L.o_counter = take(4);
   L.o_status = take(4);
-  L.o_flags = take(4 * 3 * n);
+  L.o_flags = take(4 * 4 * n);
   L.o_epoch = take(4);
   L.o_done = take(4 * 2 * D);
   const size_t ser = 8 * KC * n * D;
@@ -497,7 +497,7 @@ mdn_status mdn_load_system(mdn_ctx* ctx, int M, const int32_t* eq, const int32_t
   CU(put(L.o_occ, ctx->occ.data(), 4 * ctx->occ.size()));
   CU(cudaMemsetAsync(ctx->ws + L.o_counter, 0, 4, st));
   CU(cudaMemsetAsync(ctx->ws + L.o_status, 0, 4, st));
-  CU(cudaMemsetAsync(ctx->ws + L.o_flags, 0, 4 * 3 * (size_t)ctx->n, st));
+  CU(cudaMemsetAsync(ctx->ws + L.o_flags, 0, 4 * 4 * (size_t)ctx->n, st));
   CU(cudaMemsetAsync(ctx->ws + L.o_epoch, 0, 4, st));
   CU(cudaMemsetAsync(ctx->ws + L.o_dx, 0, 8 * (size_t)ctx->K * ctx->C * ctx->n * ctx->D, st));
   CU(cudaStreamSynchronize(st));  // host tables may be reused after return
@@ -925,12 +925,24 @@ mdn_status mdn_adjoint(mdn_ctx* ctx, const double* x, const double* g, double* g
   double* W = ctx->at<double>(L.o_W);
   double* lam = ctx->at<double>(L.o_dx);
   mdn_status r;
-  if ((r = run_a0(ctx, x, n * D, ctx->D, A, DNN, ctx->stream)) != MDN_OK) return r;
-  if ((r = run_evaluate(ctx, x, f, A, ctx->num_sms)) != MDN_OK) return r;
-  ph_begin(ctx, MDN_PHASE_QR);
-  if ((r = run_qr(ctx, A, DNN, W, ctx->stream)) != MDN_OK) return r;
-  ph_end(ctx, MDN_PHASE_QR, 3);
-  if ((r = run_forward(ctx, A, A, DNN, W, g, +1, lam, nullptr, nullptr, ctx->num_sms, true)) != MDN_OK) return r;
+  // A_0 and its QR on the side stream beside the evaluation of A(t)
+  const int qb = qr_blocks(ctx);
+  const bool overlap = ctx->side && qb <= (ctx->num_sms * 3) / 8;
+  cudaStream_t qs = overlap ? ctx->side : ctx->stream;
+  double* A0 = ctx->at<double>(L.o_A0b);
+  if (overlap) {
+    CU(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  }
+  ph_begin(ctx, MDN_PHASE_QR, qs);
+  if ((r = run_a0(ctx, x, n * D, ctx->D, A0, n * n, qs)) != MDN_OK) return r;
+  if ((r = run_qr(ctx, A0, n * n, W, qs)) != MDN_OK) return r;
+  ph_end(ctx, MDN_PHASE_QR, 5, qs);
+  if (overlap) CU(cudaEventRecord(ctx->ev_join, ctx->side));
+  // A_1..A_d (the solve with J^T reads A_0 from the QR's copy)
+  if ((r = run_evaluate(ctx, x, f, A, overlap ? ctx->num_sms - qb : ctx->num_sms)) != MDN_OK) return r;
+  if (overlap) CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+  if ((r = run_forward(ctx, A, A0, n * n, W, g, +1, lam, nullptr, nullptr, ctx->num_sms, true)) != MDN_OK) return r;
   AdjParams a{};
   a.n = ctx->n;
   a.D = ctx->D;

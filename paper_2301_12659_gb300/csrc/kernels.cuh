@@ -463,7 +463,37 @@ __device__ __forceinline__ void qr_apply_la(const QrParams& p, int j, double* y,
   __syncwarp();
 }
 
+// y -= tau_j w v_j over rows j..n-1 (w formed before tau_j was out).
+template <int K, int C>
+__device__ __forceinline__ void qr_update(const QrParams& p, int j, double* y, const cmd<K, C>& w) {
+  const int lane = threadIdx.x & 31;
+  const int n = p.n;
+  cmd<K, C> vj0, g, ng;
+  ld(p.v0, p.n, j, vj0);
+  double tau[K];
+  ld_real(p.tau, p.n, j, tau);
+  cmd_scale(w, tau, g);
+  md_neg(g.re, ng.re);
+  md_neg(g.im, ng.im);
+  __syncwarp();
+  for (int i = j + lane; i < n; i += 32) {
+    cmd<K, C> v, yi;
+    if (i == j) v = vj0;
+    else ld(p.Vm, p.Nnn, (long long)i * n + j, v);
+    ld(y, n, i, yi);
+    CAcc<K, C> b;
+    cacc_set(b, yi);
+    cacc_fma(b, ng, v);
+    cacc_get(b, yi);
+    st(y, n, i, yi);
+  }
+  __syncwarp();
+}
+
 // Column warp c: its column under the reflectors 0..c-1, then reflector c.
+// Reflector j is applied in three parts: the dot product x_j^H y as soon as
+// x_j is out (col[j]), w = dot + conj(s_j|x_j|) y[j] as soon as s_j|x_j| and
+// v_jj are out (alpha[j]), and y -= tau_j w v_j once tau_j is out (ref[j]).
 template <int K, int C>
 __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
   const int lane = threadIdx.x & 31;
@@ -471,6 +501,7 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
   unsigned* fcol = p.flags;
   unsigned* fref = p.flags + n;
   unsigned* frinv = p.flags + 2 * n;
+  unsigned* fal = p.flags + 3 * n;
   for (int i = lane; i < n; i += 32) {
     cmd<K, C> v;
     ld(p.A0, p.NA, (long long)i * n + c, v);
@@ -486,8 +517,19 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
     if (!warp_wait(&fcol[j], ep, p.spin_limit, p.status)) return;
     cmd<K, C> dot;
     qr_lookahead<K, C>(p, j, y, dot);
+    if (!warp_wait(&fal[j], ep, p.spin_limit, p.status)) return;
+    cmd<K, C> w;
+    {
+      cmd<K, C> sa, yj;
+      ld(p.salpha, p.n, j, sa);
+      ld(y, n, j, yj);
+      CAcc<K, C> a;
+      cacc_set(a, dot);
+      cacc_fma_conj(a, sa, yj);
+      cacc_get(a, w);
+    }
     if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
-    qr_apply_la<K, C>(p, j, y, dot);
+    qr_update<K, C>(p, j, y, w);
     cmd<K, C> v, nv;
     ld(y, n, j, v);
     if (lane == 0) st(p.Rm, p.Nnn, (long long)j * n + c, v);  // R[j][c] is final
@@ -555,6 +597,11 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
     cmd_scale(sg, alpha, salpha);
   }
   cmd_add(x0, salpha, v0);
+  if (lane == 0) {
+    st(p.salpha, p.n, c, salpha);
+    st(p.v0, p.n, c, v0);
+  }
+  warp_publish(&fal[c], ep);  // the later columns form their w meanwhile
   double t1[K], t2[K], tau[K];
   md_mul(alpha, ax0, t1);
   md_add(N, t1, t2);
@@ -564,8 +611,6 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
     if (lane == 0) atomicOr(p.status, MDN_DEV_SINGULAR);
   }
   if (lane == 0) {
-    st(p.salpha, p.n, c, salpha);
-    st(p.v0, p.n, c, v0);
     st_real(p.tau, p.n, c, tau);
     cmd<K, C> r;
     md_neg(salpha.re, r.re);

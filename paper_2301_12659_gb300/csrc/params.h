@@ -99,7 +99,7 @@ struct QrParams {
   double* rinv;    // [K][C][n]
   double* salpha;  // [K][C][n] s_j |x_j| (R_jj = -salpha_j)
   double* v0;      // [K][C][n] leading entry of reflector j
-  unsigned* flags;  // [3n]: column published, reflector published, 1/R_jj published
+  unsigned* flags;  // [4n]: column, reflector (tau), 1/R_jj, and s_j|x_j| with v_jj published
   const unsigned* epoch;
   int* status;
   long long spin_limit;  // nanoseconds a flag wait may last

@@ -704,13 +704,9 @@ static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, l
   CU(cudaMemsetAsync(u.rdone, 0, 4 * 2 * (size_t)ctx->D, ctx->stream));
   CU(ctx->kt->stage0(u, ctx->stream));
   if (e0) CU(cudaEventRecord(e0, ctx->stream));
-  if (ctx->D > 1) {
-    CU(ctx->kt->fsub(u, ctx->stream));
-  } else {
-    // residual of the single stage
-    u.first_stage = 1;
-    CU(ctx->kt->fsub(u, ctx->stream));
-  }
+  // stages 1..nst-1 and the residuals of all stages (with one stage, the
+  // residual of stage 0 alone)
+  CU(ctx->kt->fsub(u, ctx->stream));
   ph_end(ctx, MDN_PHASE_FORWARD, 3);
   return MDN_OK;
 }

@@ -78,10 +78,14 @@ typedef enum {
  * and rows in shared memory (a warp per column of A0 and of the identity, a
  * warp per two rows of R^{-1}; all 5n/8 blocks resident, one per SM). */
 #define MDN_MAX_N 192
+/* Largest n of a context that only evaluates (mdn_evaluate, mdn_get_residual;
+ * mdn_newton, mdn_solve and mdn_adjoint return MDN_EINVAL above MDN_MAX_N). */
+#define MDN_MAX_N_EVAL 4096
 
 /* Create a context for K limbs (2, 4 or 8; 1 runs plain doubles), real
  * (is_complex = 0) or complex (1) data, 1 <= n <= MDN_MAX_N equations and
- * unknowns and truncation degree 0 <= degree <= MDN_MAX_DEGREE.  *out receives the context
+ * unknowns (up to MDN_MAX_N_EVAL for a context that only evaluates) and
+ * truncation degree 0 <= degree <= MDN_MAX_DEGREE.  *out receives the context
  * (host memory); MDN_EINVAL on bad sizes, MDN_ECUDA without a usable GPU. */
 mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degree);
 
@@ -157,7 +161,8 @@ mdn_status mdn_set_late_updates(mdn_ctx* ctx, int first_stage, int limbs);
  * factorization.  The evaluation, the forward substitution and the update
  * skip the inactive coefficients; the norms of res_hist are over the active
  * ones, and a tolerance stops only at full order.  first_steps = 0 (default)
- * restores the plain method. */
+ * restores the plain method.  mdn_newton returns MDN_EINVAL for staggered
+ * orders when a monomial has more than 64 variables. */
 mdn_status mdn_set_stagger(mdn_ctx* ctx, int first_steps);
 
 /* Sampled residual monitor (Section 5.4 suggests the residuals of one or a

@@ -37,6 +37,9 @@ const KernelTable* kernels_for(int K, int C) {
   return nullptr;
 }
 
+// Largest monomial for which the schedules of every product length are built.
+constexpr int STAGGER_KMAX = 64;
+
 // Bounded waits of the dataflow kernels: two seconds of wall time at most.
 constexpr long long SPIN_LIMIT = 2000000000LL;
 
@@ -127,33 +130,42 @@ static void build_schedule(int k, int G, std::vector<int4>& waves_out, int& nwav
   std::vector<int> longest(nt, 1);
   for (int i = nt - 1; i >= 0; --i)
     for (int d : T[i].deps) longest[d] = std::max(longest[d], longest[i] + 1);
-  std::vector<int> done(nt, 0);
-  int ndone = 0;
+  // list scheduling: each wave takes the G ready tasks of longest chain (ties
+  // by index); tasks that become ready join the next wave
+  std::vector<std::vector<int>> dependents(nt);
+  std::vector<int> indeg(nt, 0);
+  for (int i = 0; i < nt; ++i) {
+    indeg[i] = (int)T[i].deps.size();
+    for (int d : T[i].deps) dependents[d].push_back(i);
+  }
+  auto later = [&](int a, int b) { return longest[a] != longest[b] ? longest[a] < longest[b] : a > b; };
+  std::vector<int> heap;  // max-heap under `later`
+  for (int i = 0; i < nt; ++i)
+    if (indeg[i] == 0) heap.push_back(i);
+  std::make_heap(heap.begin(), heap.end(), later);
   nwaves = 0;
-  while (ndone < nt) {
-    std::vector<int> ready;
-    for (int i = 0; i < nt; ++i) {
-      if (done[i]) continue;
-      bool ok = true;
-      for (int d : T[i].deps) ok = ok && done[d] == 1;
-      if (ok) ready.push_back(i);
+  std::vector<int> wave;
+  while (!heap.empty()) {
+    wave.clear();
+    while ((int)wave.size() < G && !heap.empty()) {
+      std::pop_heap(heap.begin(), heap.end(), later);
+      wave.push_back(heap.back());
+      heap.pop_back();
     }
-    std::stable_sort(ready.begin(), ready.end(), [&](int a, int b) { return longest[a] > longest[b]; });
-    const int take = std::min<int>(G, (int)ready.size());
     for (int g = 0; g < G; ++g) {
-      if (g < take) {
-        const Task& t = T[ready[g]];
+      if (g < (int)wave.size()) {
+        const Task& t = T[wave[g]];
         waves_out.push_back(make_int4(t.type, t.dst, t.a, t.b));
       } else {
         waves_out.push_back(make_int4(OP_NONE, 0, 0, 0));
       }
     }
-    for (int g = 0; g < take; ++g) done[ready[g]] = 2;  // finished at the end of this wave
-    for (int i = 0; i < nt; ++i)
-      if (done[i] == 2) {
-        done[i] = 1;
-        ++ndone;
-      }
+    for (int i : wave)  // finished at the end of this wave
+      for (int d : dependents[i])
+        if (--indeg[d] == 0) {
+          heap.push_back(d);
+          std::push_heap(heap.begin(), heap.end(), later);
+        }
     ++nwaves;
   }
 }
@@ -182,6 +194,7 @@ struct mdn_ctx {
       pair_slot, occ;
   std::vector<int4> sched;
   bool loaded = false, has_series = false;
+  bool solves = true;  // n small enough for the QR of A0 (else evaluation only)
   int late_stage = 1 << 30;  // stages from here form their updates in K/2 limbs
   int res_rows = 0;          // rows of the sampled residual monitor (0: all)
   int stagger_first = 0;     // staggered orders: order-1 steps with a QR each (0: off)
@@ -287,10 +300,12 @@ static mdn_status build_tables(mdn_ctx* ctx, int M, const int32_t* eq, const int
                    [&](int a, int b) { return ctx->mono_k[a] > ctx->mono_k[b]; });
   // schedules for every size 1..kmax and every lane-group count G that a
   // product length 1..D uses (G(len) = 32 / ceil(len/2); shorter lengths run
-  // with staggered orders)
+  // with staggered orders); with monomials of more than STAGGER_KMAX
+  // variables only the full length (the tables grow with G * kmax^2)
   ctx->gvals.clear();
-  ctx->gidx_of_len.assign(ctx->D + 1, 0);
+  ctx->gidx_of_len.assign(ctx->D + 1, -1);
   for (int len = 1; len <= ctx->D; ++len) {
+    if (kmax > STAGGER_KMAX && len != ctx->D) continue;
     const int g = 32 / ((len + 1) / 2);
     int gi = (int)(std::find(ctx->gvals.begin(), ctx->gvals.end(), g) - ctx->gvals.begin());
     if (gi == (int)ctx->gvals.size()) ctx->gvals.push_back(g);
@@ -411,15 +426,14 @@ mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degre
   *out = nullptr;
   const int C = is_complex ? 2 : 1;
   const KernelTable* kt = kernels_for(limbs, C);
-  if (!kt || n < 1 || n > MDN_MAX_N || degree < 0 || degree > MDN_MAX_DEGREE) return MDN_EINVAL;
-  // the QR keeps its columns and rows in shared memory, its blocks all resident
-  if (qr_smem_bytes(n, limbs) > (size_t)QR_SMEM_MAX) return MDN_EINVAL;
+  if (!kt || n < 1 || n > MDN_MAX_N_EVAL || degree < 0 || degree > MDN_MAX_DEGREE) return MDN_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MDN_ECUDA;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MDN_ECUDA;
-  // the cooperative QR launch holds all its blocks, one per SM
-  if (qr_blocks_for(n) > sms) return MDN_EINVAL;
+  // the QR keeps its columns and rows in shared memory with all its blocks
+  // resident, one per SM: beyond that size a context only evaluates
+  const bool solves = n <= MDN_MAX_N && qr_smem_bytes(n, limbs) <= (size_t)QR_SMEM_MAX && qr_blocks_for(n) <= sms;
   mdn_ctx* ctx = new (std::nothrow) mdn_ctx();
   if (!ctx) return MDN_EINVAL;
   ctx->K = limbs;
@@ -429,6 +443,7 @@ mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degre
   ctx->D = degree + 1;
   ctx->kt = kt;
   ctx->num_sms = sms;
+  ctx->solves = solves;
   ctx->P = (ctx->D + 1) / 2;  // lanes per product: coefficient pairs (k, D-1-k)
   ctx->G = 32 / ctx->P;       // products in flight per warp
   // one evaluation warp per SM sub-partition: four warps already fill an SM's
@@ -572,6 +587,7 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
   const long long D = ctx->D, n = ctx->n;
   if (len <= 0 || len > ctx->D) len = ctx->D;
   const int gi = ctx->gidx_of_len[len];
+  if (gi < 0) return fail(ctx, MDN_EINVAL, "no product schedule for %d coefficients", len);
   EdParams e{};
   e.n = ctx->n;
   e.D = ctx->D;
@@ -840,6 +856,9 @@ mdn_status mdn_newton(mdn_ctx* ctx, int max_steps, double tol, int* steps_done, 
   if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
   if (!ctx->has_series) return fail(ctx, MDN_ESTATE, "no series set");
   if (max_steps < 1 || max_steps > MDN_MAX_STEPS) return fail(ctx, MDN_EINVAL, "max_steps out of range");
+  if (!ctx->solves) return fail(ctx, MDN_EINVAL, "n = %d > MDN_MAX_N: this context only evaluates", ctx->n);
+  if (ctx->stagger_first > 0 && ctx->kmax > STAGGER_KMAX)
+    return fail(ctx, MDN_EINVAL, "staggered orders need monomials of at most %d variables", STAGGER_KMAX);
   const Layout& L = ctx->L;
   double* hist = ctx->at<double>(L.o_hist);
   CU(cudaMemsetAsync(ctx->at<int>(L.o_status), 0, 4, ctx->stream));
@@ -877,6 +896,7 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
   if (!ctx) return MDN_EINVAL;
   if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
   if (!A || !b || !dx) return fail(ctx, MDN_EINVAL, "null pointer argument");
+  if (!ctx->solves) return fail(ctx, MDN_EINVAL, "n = %d > MDN_MAX_N: this context only evaluates", ctx->n);
   CU(cudaMemsetAsync(ctx->at<int>(ctx->L.o_status), 0, 4, ctx->stream));
   const long long DNN = (long long)ctx->D * ctx->n * ctx->n;
   double* W = ctx->at<double>(ctx->L.o_W);
@@ -913,6 +933,7 @@ mdn_status mdn_adjoint(mdn_ctx* ctx, const double* x, const double* g, double* g
   if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
   if (!x || !g || !grad_out) return fail(ctx, MDN_EINVAL, "null pointer argument");
   if (ctx->C != 1) return fail(ctx, MDN_EINVAL, "the adjoint is defined for real data");
+  if (!ctx->solves) return fail(ctx, MDN_EINVAL, "n = %d > MDN_MAX_N: this context only evaluates", ctx->n);
   const Layout& L = ctx->L;
   const long long n = ctx->n, D = ctx->D, DNN = D * n * n;
   CU(cudaMemsetAsync(ctx->at<int>(L.o_status), 0, 4, ctx->stream));

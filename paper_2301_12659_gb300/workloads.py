@@ -351,3 +351,32 @@ def batch_planted_systems(cfg: BatchConfig, count: Optional[int] = None):
                       meta={"diag_monomials": np.asarray(diag, dtype=np.int32)})
         out.append((sysm, xstar, x0))
     return out
+
+
+# ---------------------------------------------------------------------------
+# the paper's one-column systems (evaluation-only context workload)
+# ---------------------------------------------------------------------------
+def one_column_system(n: int, d: int, K: int, C: int = 1, index: int = 5, delta: float = 0.1):
+    """One column of monomials with a lower triangular exponent matrix of
+    ones (Section 3): equation i is x_0 x_1 ... x_i = b_i(t), monomial i has
+    the i+1 variables 0..i and the constant coefficient series 1.  Returns
+    (System with a zero constant term, x) where x_v(t) = exp(alpha_v t)
+    truncated at degree d, alpha_v uniform in [-1, -1+delta] or [1-delta, 1],
+    held in the leading limb (the series the paper evaluates at; the
+    products of such series stay of moderate size).  Used to time the
+    evaluation and differentiation the way the paper's Table 5 does."""
+    D = d + 1
+    seed = BASE_SEED + index
+    eq = np.arange(n, dtype=np.int32)
+    vptr = np.concatenate([[0], np.cumsum(np.arange(1, n + 1))]).astype(np.int32)
+    vidx = np.concatenate([np.arange(i + 1) for i in range(n)]).astype(np.int32)
+    coeff = np.zeros((K, C, n, D))
+    coeff[0, 0, :, 0] = 1.0
+    u = 0.5 * (uniform_pm1(substream_seed(seed, 1), 2 * n) + 1.0)
+    alpha = (1.0 - delta * u[:n]) * np.where(u[n:] < 0.5, -1.0, 1.0)
+    x = np.zeros((K, C, n, D))
+    for j in range(D):
+        x[0, 0, :, j] = alpha ** j / math.factorial(j)
+    sysm = System(K, C, n, d, eq, vptr, vidx, coeff, np.zeros((K, C, n, D)), f"one-column-n{n}-d{d}-K{K}")
+    sysm.check()
+    return sysm, x

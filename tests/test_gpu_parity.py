@@ -297,3 +297,29 @@ def test_staggered_newton_matches_oracle(md, K, C, n, d, first, steps):
     nw.newton(2)
     x2_ref, _ = oracle.newton(s, x0, 2)
     assert np.max(mt.series_rel_error(to_np(nw.series()), x2_ref)) <= TOL[K]
+
+
+def test_evaluation_only_context_beyond_the_qr_limit(md):
+    """n = 300 > MDN_MAX_N: the paper's one-column system (monomial i =
+    x_0...x_i, up to 300 variables) evaluates, rows of f and of the Jacobian
+    match the oracle; the solve calls refuse.  Quad double: a product of 60
+    series of mixed-sign exponentials cancels by ~1e4, which a double double
+    result shows at its last digits (2e-28 against 1e-28)."""
+    K, n, d = 4, 300, 11
+    s, x = wl.one_column_system(n, d, K)
+    nw = _newton(md, s)
+    f, A = nw.evaluate(x)
+    f, A = to_np(f), to_np(A)
+    rows = [0, 7, 60]
+    keep = np.isin(s.eq, rows)
+    sub = wl.System(s.K, s.C, s.n, s.d, s.eq[keep], None, None, s.coeff[:, :, keep], s.cst)
+    sizes = np.diff(s.vptr)[keep]
+    sub.vptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    sub.vidx = np.concatenate([s.vidx[s.vptr[m]:s.vptr[m + 1]] for m in np.nonzero(keep)[0]]).astype(np.int32)
+    f_ref, A_ref = oracle.evaluate(sub, x)
+    assert mt.matrix_rel_error(f[:, :, rows], f_ref[:, :, rows]) <= TOL[K]
+    assert mt.matrix_rel_error(A[:, :, :, rows], A_ref[:, :, :, rows]) <= TOL[K]
+    nw.set_series(x)
+    with pytest.raises(md.MdnError) as e:
+        nw.newton(1)
+    assert e.value.status == md.MDN_EINVAL

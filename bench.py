@@ -49,6 +49,14 @@ FP64_PEAK_OPS = NUM_SMS * FP64_LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
 METRIC = "Newton steps/s (qd, n=64, d=31)"
 
 
+def metric_of(cfg) -> str:
+    """The metric name: the quad double workload's own, else named by its sizes."""
+    if cfg.name == "qd-real-n64-d31":
+        return METRIC
+    prec = {1: "d", 2: "dd", 4: "qd", 8: "od"}[cfg.K] + (" complex" if cfg.C == 2 else "")
+    return f"Newton steps/s ({prec}, n={cfg.n}, d={cfg.d})"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -188,7 +196,7 @@ def run_reference(args, cfg):
     v = args.steps / total
     cores = oracle.get_threads()
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": metric_of(cfg), "value": v, "unit": "steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(cfg),
         "data": "synthetic", "config": config_dict(cfg, args),
@@ -466,7 +474,7 @@ def run_ours(args, cfg):
     achieved = per_phase_ops[dom] / (dom_launch_ms * 1e-3)
     eval_ms = share["evaluate"] / steps_timed
     line = {
-        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "metric": metric_of(cfg), "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(cfg), "data": "synthetic",
         "config": config_dict(cfg, args),

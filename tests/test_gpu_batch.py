@@ -125,3 +125,28 @@ def test_batch_qd_4096(md):
         x_ref, _ = oracle.newton(s, items[q][2], int(steps[q]))
         assert np.max(mt.series_rel_error(xs[q], x_ref)) <= cfg.tol, q
     b.close()
+
+
+def test_batch_flags_singular_and_nonfinite_systems(md):
+    """A system whose A_0 has a zero column stops with the singular flag and a
+    system started from a NaN stops with the non-finite flag; the others of
+    the same launch still converge."""
+    items = _mixed(2, 1, SHAPES[:3], 690)
+    systems = [s for s, _, _, _ in items]
+    x0s = [x0.copy() for _, _, x0, _ in items]
+    # system 0: zero the constant coefficient of every monomial containing x_1
+    s0 = systems[0]
+    s0.coeff = s0.coeff.copy()
+    for m in range(s0.M):
+        if 1 in s0.vidx[s0.vptr[m]:s0.vptr[m + 1]]:
+            s0.coeff[:, :, m, 0] = 0.0
+    # system 1: a NaN in the start series
+    x0s[1][0, 0, 0, 0] = np.nan
+    b = md.Batch(systems)
+    x, steps, flags = b.solve(b.pack(x0s), 12, TOL[2])
+    assert flags[0] & md.BATCH_SINGULAR
+    assert flags[1] & md.BATCH_NONFINITE
+    assert flags[2] == md.BATCH_CONVERGED
+    x_ref, _ = oracle.newton(systems[2], x0s[2], int(steps[2]))
+    assert np.max(mt.series_rel_error(b.unpack(x)[2], x_ref)) <= TOL[2]
+    b.close()

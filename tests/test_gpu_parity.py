@@ -323,3 +323,21 @@ def test_evaluation_only_context_beyond_the_qr_limit(md):
     with pytest.raises(md.MdnError) as e:
         nw.newton(1)
     assert e.value.status == md.MDN_EINVAL
+
+
+def test_newton_at_the_largest_n(md):
+    """n = MDN_MAX_N = 192 (the QR launch at its largest: 120 blocks, one per
+    SM): Newton against the oracle and the plant; one past the evaluation
+    limit is refused at creation."""
+    cfg = wl.small_config(2, 1, n=192, d=3, mono_per_eq=1, kmin=1, kmax=2, steps=5, index=512)
+    s, xstar, x0 = planted(cfg)
+    x_ref, _ = oracle.newton(s, x0, cfg.steps)
+    nw = _newton(md, s)
+    nw.set_series(x0)
+    nw.newton(cfg.steps)
+    x = to_np(nw.series())
+    assert np.max(mt.series_rel_error(x, x_ref)) <= cfg.tol
+    assert np.max(mt.series_rel_error(x, xstar)) <= cfg.tol
+    with pytest.raises(md.MdnError) as e:
+        md.mdn_create(2, 0, 4097, 3)
+    assert e.value.status == md.MDN_EINVAL

@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="qd-real-n64-d31", choices=sorted(wl.CONFIGS))
     ap.add_argument("--e2e-solves", type=int, default=5)
-    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-steps", type=int, default=14)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", default="on", choices=["on", "off"],
                     help="also time the batched workload (4096 quad double systems) and the same systems one by one")

@@ -361,7 +361,14 @@ def run_adjoint(args, dev):
     torch.cuda.synchronize()
     _, phase_ms, _ = md.mdn_profile(nw.ctx, 0)
     ms = e0.elapsed_time(e1) / reps
+    counts = F.adjoint_counts(s.monomial_sizes(), s.n, s.D, s.K, s.C)
+    qr_ms = float(phase_ms[md.PHASES.index("qr")]) / reps
     out = {"workload": acfg.name, "gradients_per_s": 1e3 / ms, "ms_per_gradient": ms,
+           "roofline": {"bound": "alu", "fp64_ops_per_gradient": counts["fp64_ops"],
+                        "frac": counts["fp64_ops"] / (ms * 1e-3) / FP64_PEAK_OPS,
+                        "dominant_kernel": "qr",
+                        "qr_frac": counts["qr_fp64_ops"] / (qr_ms * 1e-3) / FP64_PEAK_OPS if qr_ms > 0 else None,
+                        "peak": FP64_PEAK_OPS / 1e12, "unit": "FP64 Tops/s"},
            "gradient_entries": int(grad.numel() // acfg.K), "loss_leading": float(loss[0]),
            "phases_ms_per_gradient": {p: float(v) / reps for p, v in zip(md.PHASES, phase_ms)}}
     nw.close()

@@ -113,3 +113,16 @@ def step_counts(sizes, n: int, D: int, K: int, C: int) -> dict:
     return {"evaluate": e, "solve": s,
             "fp64_ops": e["fp64_ops"] + s["qr_fp64_ops"] + s["forward_fp64_ops"],
             "paper_flops": e["paper_flops"] + s["paper_flops"]}
+
+
+def adjoint_counts(sizes, n: int, D: int, K: int, C: int) -> dict:
+    """One gradient: the evaluation of A(t), the QR and inverse of A_0, the
+    transposed forward substitution, and per monomial of k variables k-1
+    products of its variables plus one correlation (D(D+1)/2 multiply-adds)."""
+    s = step_counts(sizes, n, D, K, C)
+    o = cmd_ops(K, C)
+    tri = D * (D + 1) // 2
+    sizes = np.asarray(sizes)
+    corr = int(sum(max(0, int(k) - 1) + 1 for k in sizes))
+    adj = corr * (tri * o["acc_fma"] + D * o["acc_get"])
+    return {"fp64_ops": s["fp64_ops"] + adj, "qr_fp64_ops": s["solve"]["qr_fp64_ops"], "correlation_fp64_ops": adj}

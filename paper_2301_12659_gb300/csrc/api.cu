@@ -789,8 +789,9 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
     if ((r = run_evaluate(ctx, x, f, A, rest, len)) != MDN_OK) return r;
     if (overlap) CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     const bool next = s + 1 < steps && qr_at(ctx, s + 1);
+    // with no QR to run beside it the forward substitution takes every SM
     if ((r = run_forward(ctx, A, A0b[b], nn, Wb[b], f, -1, dx, x, (overlap && next) ? ctx->ev_fork : nullptr,
-                         rest, false, len)) != MDN_OK)
+                         (overlap && next) ? rest : ctx->num_sms, false, len)) != MDN_OK)
       return r;
     if (next) {
       // A_0 and QR of step s+1 from x_0 + dx_0

@@ -1,6 +1,11 @@
-// Kernels of libmdnewton for K = 1 limbs, C = 1 (one translation unit per
-// instantiation so the library builds in parallel).
+// Kernels of libmdnewton for K = 1 limbs, C = 1.  Each instantiation is
+// split over three translation units that build in parallel: this one (the
+// table, evaluation, forward substitution and the rest), the QR of A_0 in
+// inst_k1_c1_qr.cu and the batched solver in inst_k1_c1_batch.cu.
 #include "batch.cuh"
 namespace mdn {
+extern template cudaError_t launch_qr<1, 1>(const QrParams&, cudaStream_t);
+extern template cudaError_t launch_batch<1, 1>(const BatchParams&, int, int, cudaStream_t);
+extern template int batch_occupancy<1, 1>(int);
 const KernelTable* kernels_k1_c1() { return make_table<1, 1>(); }
 }  // namespace mdn

@@ -1,0 +1,7 @@
+// The batched solver's kernel for K = 4 limbs, C = 2 (a translation unit of
+// its own so that it compiles beside the other kernels of this instantiation).
+#include "batch.cuh"
+namespace mdn {
+template cudaError_t launch_batch<4, 2>(const BatchParams&, int, int, cudaStream_t);
+template int batch_occupancy<4, 2>(int);
+}  // namespace mdn

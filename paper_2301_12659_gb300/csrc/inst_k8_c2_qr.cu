@@ -1,0 +1,5 @@
+// The QR of A_0 (qr_kernel, w_kernel) for K = 8 limbs, C = 2.
+#include "batch.cuh"
+namespace mdn {
+template cudaError_t launch_qr<8, 2>(const QrParams&, cudaStream_t);
+}  // namespace mdn

@@ -22,6 +22,7 @@
 #include <cstdint>
 #include "md.cuh"
 #include "params.h"
+#include "xf.cuh"
 
 namespace mdn {
 
@@ -397,95 +398,189 @@ __global__ void a0_assemble_kernel(A0Params p) {
 // |a_c|^2 - sum_{i<=j} |R_ic|^2 (a_c = column c of A0), accumulated as each
 // R_ic becomes final and recomputed directly if more than 8 bits cancel.
 
+// All arithmetic of the three roles runs in integer-limb extended floats
+// (xf.cuh): on this part a warp's FP64 instruction occupies its sub-partition
+// for 64 cycles, so a dependent chain of md operations on one warp is bound
+// by the FP64 issue rate, while the same values carried in 64-bit integer
+// words (64W >= 53K + 11 bits) move on the integer pipe.  Columns and rows
+// stay in shared and global memory as md values (K limbs); they are
+// converted to xf where they are read and rounded back to K limbs where they
+// are stored, so every stored value is an md value correct to its precision.
+
+// complex (or real, C = 1) extended floats
+template <int W, int C>
+struct cxf {
+  xfn::xf<W> re, im;
+};
+
+template <int K, int W, int C>
+__device__ __forceinline__ void cxf_load(const double* p, long long N, long long i, cxf<W, C>& v) {
+  cmd<K, C> t;
+  ld(p, N, i, t);
+  xfn::xf_from_md<K, W>(t.re, v.re);
+  if constexpr (C == 2) xfn::xf_from_md<K, W>(t.im, v.im);
+  else xfn::xf_zero(v.im);
+}
+template <int K, int W, int C>
+__device__ __forceinline__ void cxf_store(double* p, long long N, long long i, const cxf<W, C>& v) {
+  cmd<K, C> t;
+  xfn::xf_to_md<K, W>(v.re, t.re);
+  if constexpr (C == 2) xfn::xf_to_md<K, W>(v.im, t.im);
+  else md_zero(t.im);
+  st(p, N, i, t);
+}
+template <int W, int C>
+__device__ __forceinline__ void cxf_zero(cxf<W, C>& v) {
+  xfn::xf_zero(v.re);
+  xfn::xf_zero(v.im);
+}
+template <int W, int C>
+__device__ __forceinline__ void cxf_neg(cxf<W, C>& v) {
+  xfn::xf_neg(v.re);
+  xfn::xf_neg(v.im);
+}
+template <int W, int C>
+__device__ __forceinline__ void cxf_add(const cxf<W, C>& a, const cxf<W, C>& b, cxf<W, C>& r) {
+  xfn::xf_add(a.re, b.re, r.re);
+  if constexpr (C == 2) xfn::xf_add(a.im, b.im, r.im);
+  else xfn::xf_zero(r.im);
+}
+// r = a b (conj_a: conj(a) b)
+template <bool conj_a, int W, int C>
+__device__ __forceinline__ void cxf_mul(const cxf<W, C>& a, const cxf<W, C>& b, cxf<W, C>& r) {
+  using namespace xfn;
+  if constexpr (C == 1) {
+    xf_mul(a.re, b.re, r.re);
+    xf_zero(r.im);
+  } else {
+    xf<W> t1, t2, t3, t4;
+    xf_mul(a.re, b.re, t1);
+    xf_mul(a.im, b.im, t2);
+    xf_mul(a.re, b.im, t3);
+    xf_mul(a.im, b.re, t4);
+    if constexpr (conj_a) {
+      xf_add(t1, t2, r.re);
+      xf_sub(t3, t4, r.im);
+    } else {
+      xf_sub(t1, t2, r.re);
+      xf_add(t3, t4, r.im);
+    }
+  }
+}
+template <bool conj_a, int W, int C>
+__device__ __forceinline__ void cxf_fma(cxf<W, C>& acc, const cxf<W, C>& a, const cxf<W, C>& b) {
+  cxf<W, C> t;
+  cxf_mul<conj_a>(a, b, t);
+  cxf_add(acc, t, acc);
+}
+template <int W, int C>
+__device__ __forceinline__ void cxf_scale(const cxf<W, C>& a, const xfn::xf<W>& s, cxf<W, C>& r) {
+  xfn::xf_mul(a.re, s, r.re);
+  if constexpr (C == 2) xfn::xf_mul(a.im, s, r.im);
+  else xfn::xf_zero(r.im);
+}
+template <int W>
+__device__ __forceinline__ void xf_shfl_xor(const xfn::xf<W>& a, xfn::xf<W>& o, int off) {
+#pragma unroll
+  for (int i = 0; i < W; ++i) o.m[i] = __shfl_xor_sync(FULL, a.m[i], off);
+  o.e = __shfl_xor_sync(FULL, a.e, off);
+  o.s = __shfl_xor_sync(FULL, a.s, off);
+}
+template <int W>
+__device__ __forceinline__ void xf_bcast(xfn::xf<W>& a, int src) {
+#pragma unroll
+  for (int i = 0; i < W; ++i) a.m[i] = __shfl_sync(FULL, a.m[i], src);
+  a.e = __shfl_sync(FULL, a.e, src);
+  a.s = __shfl_sync(FULL, a.s, src);
+}
+// sum over the warp; every lane gets lane 0's total
+template <int W, int C>
+__device__ __forceinline__ void cxf_warp_sum(cxf<W, C>& v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    cxf<W, C> o;
+    xf_shfl_xor(v.re, o.re, off);
+    xfn::xf_add(v.re, o.re, v.re);
+    if constexpr (C == 2) {
+      xf_shfl_xor(v.im, o.im, off);
+      xfn::xf_add(v.im, o.im, v.im);
+    }
+  }
+  xf_bcast(v.re, 0);
+  if constexpr (C == 2) xf_bcast(v.im, 0);
+}
+
 // dot = sum of conj(x_j[i]) y[i] over rows i = j..n-1 (x_j from Vm).
 template <int K, int C>
-__device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const double* y, cmd<K, C>& dot) {
+__device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const double* y,
+                                             cxf<xfn::xf_words_t<K>::value, C>& dot) {
+  constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
-  CAcc<K, C> acc;
-  cacc_zero(acc);
+  cxf_zero(dot);
   for (int i = j + lane; i < n; i += 32) {
-    cmd<K, C> x, yi;
-    ld(p.Vm, p.Nnn, (long long)i * n + j, x);
-    ld(y, n, i, yi);
-    cacc_fma_conj(acc, x, yi);
+    cxf<W, C> x, yi;
+    cxf_load<K, W, C>(p.Vm, p.Nnn, (long long)i * n + j, x);
+    cxf_load<K, W, C>(y, n, i, yi);
+    cxf_fma<true>(dot, x, yi);
   }
-  warp_sum_acc(acc, dot);
+  cxf_warp_sum(dot);
 }
 
 // |y|^2 over rows i0..n-1, every lane gets it.
 template <int K, int C>
-__device__ __forceinline__ void qr_norm2(const double* y, int n, int i0, double (&nrm)[K]) {
+__device__ __forceinline__ void qr_norm2(const double* y, int n, int i0, xfn::xf<xfn::xf_words_t<K>::value>& nrm) {
+  constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
-  CAcc<K, C> ca;
-  cacc_zero(ca);
+  cxf<W, 1> acc;
+  cxf_zero(acc);
   for (int i = i0 + lane; i < n; i += 32) {
-    cmd<K, C> v;
-    ld(y, n, i, v);
-    acc_fma(ca.re, v.re, v.re);
-    if constexpr (C == 2) acc_fma(ca.re, v.im, v.im);
+    cxf<W, C> v, q;
+    cxf_load<K, W, C>(y, n, i, v);
+    cxf_mul<true>(v, v, q);
+    xfn::xf_add(acc.re, q.re, acc.re);
   }
-  cmd<K, C> t;
-  warp_sum_acc(ca, t);
-  md_copy(t.re, nrm);
+  cxf_warp_sum(acc);
+  nrm = acc.re;
 }
 
-// y -= tau_j w v_j with w = dot + conj(salpha_j) y[j] (rows j..n-1).
+// w = dot + conj(s_j|x_j|) y[j] (needs the alpha flag of reflector j)
 template <int K, int C>
-__device__ __forceinline__ void qr_apply_la(const QrParams& p, int j, double* y, const cmd<K, C>& dot) {
-  const int lane = threadIdx.x & 31;
-  const int n = p.n;
-  cmd<K, C> sa, vj0, yj, w, g, ng;
-  ld(p.salpha, p.n, j, sa);
-  ld(p.v0, p.n, j, vj0);
-  double tau[K];
-  ld_real(p.tau, p.n, j, tau);
-  ld(y, n, j, yj);
-  CAcc<K, C> a;
-  cacc_set(a, dot);
-  cacc_fma_conj(a, sa, yj);
-  cacc_get(a, w);
-  cmd_scale(w, tau, g);
-  md_neg(g.re, ng.re);
-  md_neg(g.im, ng.im);
-  __syncwarp();
-  for (int i = j + lane; i < n; i += 32) {
-    cmd<K, C> v, yi;
-    if (i == j) v = vj0;
-    else ld(p.Vm, p.Nnn, (long long)i * n + j, v);
-    ld(y, n, i, yi);
-    CAcc<K, C> b;
-    cacc_set(b, yi);
-    cacc_fma(b, ng, v);
-    cacc_get(b, yi);
-    st(y, n, i, yi);
-  }
-  __syncwarp();
+__device__ __forceinline__ void qr_form_w(const QrParams& p, int j, const double* y,
+                                          const cxf<xfn::xf_words_t<K>::value, C>& dot,
+                                          cxf<xfn::xf_words_t<K>::value, C>& w) {
+  constexpr int W = xfn::xf_words_t<K>::value;
+  cxf<W, C> sa, yj;
+  cxf_load<K, W, C>(p.salpha, p.n, j, sa);
+  cxf_load<K, W, C>(y, p.n, j, yj);
+  w = dot;
+  cxf_fma<true>(w, sa, yj);
 }
 
-// y -= tau_j w v_j over rows j..n-1 (w formed before tau_j was out).
+// y -= tau_j w v_j over rows j..n-1 (needs the ref flag of reflector j).
 template <int K, int C>
-__device__ __forceinline__ void qr_update(const QrParams& p, int j, double* y, const cmd<K, C>& w) {
+__device__ __forceinline__ void qr_update(const QrParams& p, int j, double* y,
+                                          const cxf<xfn::xf_words_t<K>::value, C>& w) {
+  constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
-  cmd<K, C> vj0, g, ng;
-  ld(p.v0, p.n, j, vj0);
-  double tau[K];
-  ld_real(p.tau, p.n, j, tau);
-  cmd_scale(w, tau, g);
-  md_neg(g.re, ng.re);
-  md_neg(g.im, ng.im);
+  xfn::xf<W> tau;
+  {
+    double t[K];
+    ld_real(p.tau, p.n, j, t);
+    xfn::xf_from_md<K, W>(t, tau);
+  }
+  cxf<W, C> ng;
+  cxf_scale(w, tau, ng);
+  cxf_neg(ng);
   __syncwarp();
   for (int i = j + lane; i < n; i += 32) {
-    cmd<K, C> v, yi;
-    if (i == j) v = vj0;
-    else ld(p.Vm, p.Nnn, (long long)i * n + j, v);
-    ld(y, n, i, yi);
-    CAcc<K, C> b;
-    cacc_set(b, yi);
-    cacc_fma(b, ng, v);
-    cacc_get(b, yi);
-    st(y, n, i, yi);
+    cxf<W, C> v, yi;
+    if (i == j) cxf_load<K, W, C>(p.v0, p.n, j, v);
+    else cxf_load<K, W, C>(p.Vm, p.Nnn, (long long)i * n + j, v);
+    cxf_load<K, W, C>(y, n, i, yi);
+    cxf_fma<false>(yi, ng, v);
+    cxf_store<K, W, C>(y, n, i, yi);
   }
   __syncwarp();
 }
@@ -496,6 +591,8 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, double* y, c
 // v_jj are out (alpha[j]), and y -= tau_j w v_j once tau_j is out (ref[j]).
 template <int K, int C>
 __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
+  using namespace xfn;
+  constexpr int W = xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   unsigned* fcol = p.flags;
@@ -509,36 +606,24 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
   }
   __syncwarp();
   // |a_c|^2, then minus |R_jc|^2 as each R_jc is final
-  double norm0[K];
+  xf<W> norm0, xN;
   qr_norm2<K, C>(y, n, 0, norm0);
-  Acc<K> nacc;
-  acc_set(nacc, norm0);
+  xN = norm0;
   for (int j = 0; j < c; ++j) {
     if (!warp_wait(&fcol[j], ep, p.spin_limit, p.status)) return;
-    cmd<K, C> dot;
+    cxf<W, C> dot, w;
     qr_lookahead<K, C>(p, j, y, dot);
     if (!warp_wait(&fal[j], ep, p.spin_limit, p.status)) return;
-    cmd<K, C> w;
-    {
-      cmd<K, C> sa, yj;
-      ld(p.salpha, p.n, j, sa);
-      ld(y, n, j, yj);
-      CAcc<K, C> a;
-      cacc_set(a, dot);
-      cacc_fma_conj(a, sa, yj);
-      cacc_get(a, w);
-    }
+    qr_form_w<K, C>(p, j, y, dot, w);
     if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
     qr_update<K, C>(p, j, y, w);
-    cmd<K, C> v, nv;
+    cmd<K, C> v;
     ld(y, n, j, v);
     if (lane == 0) st(p.Rm, p.Nnn, (long long)j * n + c, v);  // R[j][c] is final
-    md_neg(v.re, nv.re);
-    acc_fma(nacc, nv.re, v.re);
-    if constexpr (C == 2) {
-      md_neg(v.im, nv.im);
-      acc_fma(nacc, nv.im, v.im);
-    }
+    cxf<W, C> xv, q;
+    cxf_load<K, W, C>(y, n, j, xv);
+    cxf_mul<true>(xv, xv, q);
+    xf_sub(xN, q.re, xN);
   }
   // publish x_c (rows c..n-1)
   for (int i = c + lane; i < n; i += 32) {
@@ -547,65 +632,72 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
     st(p.Vm, p.Nnn, (long long)i * n + c, v);
   }
   warp_publish(&fcol[c], ep);
-  // N = |x_c|^2 by downdating (recomputed on cancellation)
-  double N[K];
-  acc_get(nacc, N);
-  if (c > 0) {
-    // more than 8 bits lost (or a negative difference): recompute
-    const unsigned long long eN = (unsigned long long)__double_as_longlong(N[0]) >> 52;
-    const unsigned long long eP = (unsigned long long)__double_as_longlong(norm0[0]) >> 52;
-    if ((__double_as_longlong(N[0]) <= 0) || (eN + 8 < eP)) qr_norm2<K, C>(y, n, c, N);
-  }
-  const bool singular = !nonzero(N[0]);
-  if (singular) N[0] = 1.0;  // keep the arithmetic finite; reported below
-  double ry[K], alpha[K];
-  md_rsqrt(N, ry);  // 1 / |x_c|
-  md_mul(N, ry, alpha);
-  cmd<K, C> x0;
-  ld(y, n, c, x0);
-  double ax0[K];
-  cmd<K, C> sg;
-  cmd_zero(sg);
+  // N = |x_c|^2 by downdating, recomputed when it is not positive or more
+  // than 8 bits cancelled
+  if (c > 0 && (xN.s != 0 || xf_is_zero(xN) || xN.e + 8 < norm0.e)) qr_norm2<K, C>(y, n, c, xN);
+  const bool singular = xf_is_zero(xN);
+  if (singular) xf_from_double(1.0, xN);  // keep the arithmetic finite; reported below
+  // The pivot scalars:
+  //   |x_c| = N / sqrt(N),  s = x_cc / |x_cc| (1 if x_cc = 0),
+  //   v_cc = x_cc + s|x_c|,  tau = 1 / (N + |x_c| |x_cc|),
+  //   R_cc = -s|x_c|,  1 / R_cc = -conj(s) / |x_c|.
+  xf<W> xry, xal, xax0;
+  xf_rsqrt(xN, xry);
+  xf_mul(xN, xry, xal);
+  cxf<W, C> x0;
+  cxf_load<K, W, C>(y, n, c, x0);
+  xf<W> sre, sim;  // s|x_c|
+  xf<W> sgr, sgi;  // s
+  bool neg = false;
   if constexpr (C == 1) {
-    const bool neg = __double_as_longlong(x0.re[0]) < 0;
-    sg.re[0] = neg ? -1.0 : 1.0;
-#pragma unroll
-    for (int l = 0; l < K; ++l) ax0[l] = neg ? -x0.re[l] : x0.re[l];
+    neg = x0.re.s != 0;
+    xax0 = x0.re;
+    xax0.s = 0;
+    sre = xal;
+    if (neg) xf_neg(sre);
+    xf_zero(sim);
   } else {
-    double a2x[K], rx[K];
-    cmd_abs2(x0, a2x);
-    const bool z = !nonzero(a2x[0]);
-    if (z) a2x[0] = 1.0;
-    md_rsqrt(a2x, rx);
-    md_mul(a2x, rx, ax0);
-    md_mul(x0.re, rx, sg.re);
-    md_mul(x0.im, rx, sg.im);
+    xf<W> t1, t2, a2x, rx;
+    xf_mul(x0.re, x0.re, t1);
+    xf_mul(x0.im, x0.im, t2);
+    xf_add(t1, t2, a2x);
+    const bool z = xf_is_zero(a2x);
+    if (z) xf_from_double(1.0, a2x);
+    xf_rsqrt(a2x, rx);
+    xf_mul(a2x, rx, xax0);
+    xf_mul(x0.re, rx, sgr);
+    xf_mul(x0.im, rx, sgi);
     if (z) {
-      md_zero(ax0);
-      cmd_zero(sg);
-      sg.re[0] = 1.0;
+      xf_zero(xax0);
+      xf_from_double(1.0, sgr);
+      xf_zero(sgi);
     }
+    xf_mul(sgr, xal, sre);
+    xf_mul(sgi, xal, sim);
   }
   cmd<K, C> salpha, v0;
-  if constexpr (C == 1) {
-    // s = +-1: s |x_c| is a sign change
-    const bool neg = sg.re[0] < 0.0;
-#pragma unroll
-    for (int l = 0; l < K; ++l) salpha.re[l] = neg ? -alpha[l] : alpha[l];
-    md_zero(salpha.im);
-  } else {
-    cmd_scale(sg, alpha, salpha);
+  {
+    xf<W> vr, vi;
+    xf_add(x0.re, sre, vr);
+    xf_add(x0.im, sim, vi);
+    xf_to_md<K, W>(sre, salpha.re);
+    xf_to_md<K, W>(sim, salpha.im);
+    xf_to_md<K, W>(vr, v0.re);
+    xf_to_md<K, W>(vi, v0.im);
   }
-  cmd_add(x0, salpha, v0);
   if (lane == 0) {
     st(p.salpha, p.n, c, salpha);
     st(p.v0, p.n, c, v0);
   }
   warp_publish(&fal[c], ep);  // the later columns form their w meanwhile
-  double t1[K], t2[K], tau[K];
-  md_mul(alpha, ax0, t1);
-  md_add(N, t1, t2);
-  md_recip(t2, tau);
+  double tau[K];
+  {
+    xf<W> t1, t2, t3;
+    xf_mul(xal, xax0, t1);
+    xf_add(xN, t1, t2);
+    xf_recip(t2, t3);
+    xf_to_md<K, W>(t3, tau);
+  }
   if (singular) {
     md_zero(tau);
     if (lane == 0) atomicOr(p.status, MDN_DEV_SINGULAR);
@@ -620,11 +712,19 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
   warp_publish(&fref[c], ep);
   // 1 / R_cc = -conj(s) / |x_c|
   cmd<K, C> rinv;
-  double nry[K];
-  md_neg(ry, nry);
-  md_mul(sg.re, nry, rinv.re);
-  if constexpr (C == 2) md_mul(sg.im, ry, rinv.im);
-  else md_zero(rinv.im);
+  if constexpr (C == 1) {
+    xf<W> rr = xry;  // s = +-1
+    if (!neg) xf_neg(rr);
+    xf_to_md<K, W>(rr, rinv.re);
+    md_zero(rinv.im);
+  } else {
+    xf<W> rr, ri;
+    xf_mul(sgr, xry, rr);
+    xf_neg(rr);
+    xf_mul(sgi, xry, ri);
+    xf_to_md<K, W>(rr, rinv.re);
+    xf_to_md<K, W>(ri, rinv.im);
+  }
   if (singular) cmd_zero(rinv);
   if (lane == 0) st(p.rinv, p.n, c, rinv);
   warp_publish(&frinv[c], ep);
@@ -633,6 +733,7 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
 // Identity warp e: Q^H e_e as the reflectors appear (column e of Y = Q^H).
 template <int K, int C>
 __device__ void qr_identity(const QrParams& p, int e, double* y, unsigned ep) {
+  constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   unsigned* fref = p.flags + n;
@@ -645,9 +746,10 @@ __device__ void qr_identity(const QrParams& p, int e, double* y, unsigned ep) {
   __syncwarp();
   for (int j = 0; j < n; ++j) {
     if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
-    cmd<K, C> dot;
+    cxf<W, C> dot, w;
     qr_lookahead<K, C>(p, j, y, dot);
-    qr_apply_la<K, C>(p, j, y, dot);
+    qr_form_w<K, C>(p, j, y, dot, w);
+    qr_update<K, C>(p, j, y, w);
   }
   for (int i = lane; i < n; i += 32) {
     cmd<K, C> v;
@@ -662,6 +764,7 @@ __device__ void qr_identity(const QrParams& p, int e, double* y, unsigned ep) {
 // the block inverse of the leading (c+1) x (c+1) part of R.
 template <int K, int C>
 __device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, double* za, double* zb, unsigned ep) {
+  constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   unsigned* frinv = p.flags + 2 * n;
@@ -677,19 +780,22 @@ __device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, double* za, doub
       if (c == i) {
         zc = rc;
       } else {
-        CAcc<K, C> acc;
-        cacc_zero(acc);
+        cxf<W, C> acc;
+        cxf_zero(acc);
         for (int k = i + lane; k < c; k += 32) {
-          cmd<K, C> zk, rk;
-          ld(z, n, k, zk);
-          ld(p.Rm, p.Nnn, (long long)k * n + c, rk);
-          cacc_fma(acc, zk, rk);
+          cxf<W, C> zk, rk;
+          cxf_load<K, W, C>(z, n, k, zk);
+          cxf_load<K, W, C>(p.Rm, p.Nnn, (long long)k * n + c, rk);
+          cxf_fma<false>(acc, zk, rk);
         }
-        cmd<K, C> s, t;
-        warp_sum_acc(acc, s);
-        cmd_mul(s, rc, t);
-        md_neg(t.re, zc.re);
-        md_neg(t.im, zc.im);
+        cxf_warp_sum(acc);
+        cxf<W, C> xr, t;
+        cxf_load<K, W, C>(p.rinv, p.n, c, xr);
+        cxf_mul<false>(acc, xr, t);
+        cxf_neg(t);
+        xfn::xf_to_md<K, W>(t.re, zc.re);
+        if constexpr (C == 2) xfn::xf_to_md<K, W>(t.im, zc.im);
+        else md_zero(zc.im);
       }
       if (lane == 0) {
         st(z, n, c, zc);

@@ -1,0 +1,492 @@
+// xf.cuh -- extended floats with 64-bit integer limbs, for the scalar chains
+// of the multiple double (md) kernels.
+//
+// On this part an FP64 warp instruction costs 64 cycles in its SM
+// sub-partition while a 32-bit integer multiply-add runs 38x faster (the
+// measured rates behind md.cuh).  A dependent chain of md operations on one
+// warp (the pivot scalars of a Householder reflector: a reciprocal square
+// root, a reciprocal, a few products) therefore waits on the FP64 pipe for
+// microseconds per operation.  An xf carries the same value with W 64-bit
+// words of mantissa and integer exponent and sign, and runs its arithmetic on
+// the integer pipe:
+//
+//   value = (-1)^s * (M / 2^(64W-1)) * 2^e,   M = m[W-1]..m[0], top bit set
+//
+// (zero: M = 0, e = XF_ZERO_E, s = 0).  W is chosen so that 64W exceeds the
+// 53K bits of a K-limb md value by at least 11 bits (xf_words_t<K>), so a
+// conversion md -> xf is exact unless gaps between the limbs make them span
+// more than 64W bits (then bits below 2^(1-64W) relative are dropped), and
+// every xf operation rounds (truncates) far below the md precision:
+//   * add/sub: operands aligned with one guard word, so a difference with
+//     cancellation is exact; error < 2^(2-64W) relative to the result;
+//   * mul: the columns of the 2W-word product below word W-2 are dropped;
+//     error < 2^(3-64W) relative;
+//   * reciprocal and reciprocal square root: Newton's iterations for 1/a
+//     and 1/sqrt(a) (y += y(1 - ay), y += y(1 - ay^2)/2), started from the
+//     double precision reciprocal / reciprocal square root of the leading
+//     53 bits and repeated until 53 * 2^iterations >= 64W;
+//   * xf -> md: K times, the leading 53 bits rounded to nearest give a limb
+//     and the exact remainder goes on, so the limbs are nonoverlapping with
+//     |limb_{l+1}| <= ulp(limb_l)/2.
+// Values must stay within the normal double range (no subnormal limbs;
+// a limb below 2^-1022 is flushed to zero).  The functions are __host__
+// __device__ so that the host build tests them against exact rationals.
+#pragma once
+#include <cstdint>
+#if !defined(__CUDA_ARCH__)
+#include <cmath>
+#include <cstring>
+#endif
+
+#if defined(__CUDACC__)
+#define XF_FN __host__ __device__ __forceinline__
+#else
+#define XF_FN inline
+#endif
+
+namespace xfn {
+
+constexpr int XF_ZERO_E = -(1 << 28);
+
+template <int K>
+struct xf_words_t {
+  static constexpr int value = K == 1 ? 1 : K == 2 ? 2 : K == 4 ? 4 : 7;
+};
+
+template <int W>
+struct xf {
+  uint64_t m[W];  // m[W-1] most significant
+  int e;
+  int s;
+};
+
+// ---------------------------------------------------------------------------
+// portable word operations
+// ---------------------------------------------------------------------------
+XF_FN uint64_t umulhi(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+XF_FN int clz64(uint64_t x) {  // x != 0
+#if defined(__CUDA_ARCH__)
+  return __clzll((long long)x);
+#else
+  return __builtin_clzll(x);
+#endif
+}
+XF_FN uint64_t dbits(double x) {
+#if defined(__CUDA_ARCH__)
+  return (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t b;
+  std::memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+XF_FN double bitsd(uint64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  std::memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+XF_FN double drecip(double x) {
+#if defined(__CUDA_ARCH__)
+  return __drcp_rn(x);
+#else
+  return 1.0 / x;
+#endif
+}
+XF_FN double drsqrt(double x) {
+#if defined(__CUDA_ARCH__)
+  return rsqrt(x);
+#else
+  return 1.0 / std::sqrt(x);
+#endif
+}
+// (hi:lo) >> b for 0 <= b < 64
+XF_FN uint64_t fshr(uint64_t lo, uint64_t hi, int b) {
+  return b == 0 ? lo : ((lo >> b) | (hi << (64 - b)));
+}
+// (hi:lo) << b, the high word, for 0 <= b < 64
+XF_FN uint64_t fshl(uint64_t lo, uint64_t hi, int b) {
+  return b == 0 ? hi : ((hi << b) | (lo >> (64 - b)));
+}
+
+// ---------------------------------------------------------------------------
+// mantissa shifts and normalisation
+// ---------------------------------------------------------------------------
+// r[0..W] = the W-word a shifted right by s >= 0 bits into W+1 words, r[0]
+// receiving the first word of bits shifted out (a guard word).
+template <int W>
+XF_FN void shr_guard(const uint64_t (&a)[W], int s, uint64_t (&r)[W + 1]) {
+  uint64_t t[W + 1];
+  t[0] = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) t[i + 1] = a[i];
+  const int q = s >> 6;
+  const int b = s & 63;
+#pragma unroll
+  for (int st = 1; st <= W; st <<= 1) {
+    const bool on = (q & st) != 0;
+#pragma unroll
+    for (int i = 0; i <= W; ++i) t[i] = on ? (i + st <= W ? t[i + st] : 0ULL) : t[i];
+  }
+  const bool gone = q > W;
+#pragma unroll
+  for (int i = 0; i <= W; ++i) {
+    const uint64_t v = fshr(t[i], i + 1 <= W ? t[i + 1] : 0ULL, b);
+    r[i] = gone ? 0ULL : v;
+  }
+}
+
+// leading zero bits of the N-word a (64N if zero)
+template <int N>
+XF_FN int lzcount(const uint64_t (&a)[N]) {
+  int lz = 64 * N;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (a[i] != 0ULL) lz = 64 * (N - 1 - i) + clz64(a[i]);
+  return lz;
+}
+
+// a <<= s for 0 <= s < 64N (in place)
+template <int N>
+XF_FN void shl_inplace(uint64_t (&a)[N], int s) {
+  const int q = s >> 6;
+  const int b = s & 63;
+#pragma unroll
+  for (int st = 1; st < N; st <<= 1) {
+    const bool on = (q & st) != 0;
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) a[i] = on ? (i - st >= 0 ? a[i - st] : 0ULL) : a[i];
+  }
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) a[i] = fshl(i > 0 ? a[i - 1] : 0ULL, a[i], b);
+}
+
+template <int W>
+XF_FN void xf_zero(xf<W>& r) {
+#pragma unroll
+  for (int i = 0; i < W; ++i) r.m[i] = 0ULL;
+  r.e = XF_ZERO_E;
+  r.s = 0;
+}
+template <int W>
+XF_FN bool xf_is_zero(const xf<W>& a) {
+  return a.m[W - 1] == 0ULL;
+}
+template <int W>
+XF_FN void xf_neg(xf<W>& a) {
+  a.s = xf_is_zero(a) ? 0 : a.s ^ 1;
+}
+
+// The W+1-word g, worth G / 2^(64W+63) * 2^e with G = sum g[i] 2^(64i),
+// normalised into r (truncated to W words), or zero.
+template <int W>
+XF_FN void xf_pack(uint64_t (&g)[W + 1], int e, int s, xf<W>& r) {
+  const int lz = lzcount<W + 1>(g);
+  const bool z = lz >= 64 * (W + 1);
+  shl_inplace<W + 1>(g, z ? 0 : lz);
+#pragma unroll
+  for (int i = 0; i < W; ++i) r.m[i] = z ? 0ULL : g[i + 1];
+  r.e = z ? XF_ZERO_E : e - lz;
+  r.s = z ? 0 : s;
+}
+
+// ---------------------------------------------------------------------------
+// arithmetic
+// ---------------------------------------------------------------------------
+// |a| < |b|
+template <int W>
+XF_FN bool mag_less(const xf<W>& a, const xf<W>& b) {
+  bool lt = false, decided = false;
+  if (a.e != b.e) {
+    lt = a.e < b.e;
+    decided = true;
+  }
+#pragma unroll
+  for (int i = W - 1; i >= 0; --i) {
+    if (!decided && a.m[i] != b.m[i]) {
+      lt = a.m[i] < b.m[i];
+      decided = true;
+    }
+  }
+  return lt;
+}
+
+template <int W>
+XF_FN void xf_add(const xf<W>& a, const xf<W>& b, xf<W>& r) {
+  const bool sw = mag_less(a, b);
+  const xf<W>& x = sw ? b : a;  // larger magnitude
+  const xf<W>& y = sw ? a : b;
+  const int d = x.e - y.e;  // >= 0 (zero has the least exponent)
+  uint64_t ys[W + 1];
+  shr_guard<W>(y.m, d, ys);
+  uint64_t g[W + 2];
+  if (x.s == y.s) {
+    uint64_t c = 0;
+    g[0] = ys[0];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const uint64_t u = x.m[i] + ys[i + 1];
+      const uint64_t c1 = u < x.m[i];
+      const uint64_t v = u + c;
+      c = c1 | (v < u);
+      g[i + 1] = v;
+    }
+    g[W + 1] = c;
+  } else {
+    uint64_t bw = 0;
+    // guard word of x is zero
+    {
+      const uint64_t v = 0ULL - ys[0];
+      bw = ys[0] != 0ULL;
+      g[0] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const uint64_t u = x.m[i] - ys[i + 1];
+      const uint64_t b1 = x.m[i] < ys[i + 1];
+      const uint64_t v = u - bw;
+      bw = b1 | (u < bw);
+      g[i + 1] = v;
+    }
+    g[W + 1] = 0ULL;
+  }
+  // g (W+2 words) has its leading bit at 64(W+1) or below; the value is
+  // g / 2^(64W+63) * 2^(x.e) with the top bit of word W+1 worth 2^(x.e+1)
+  uint64_t h[W + 1];
+  const bool carry = g[W + 1] != 0ULL;
+#pragma unroll
+  for (int i = 0; i <= W; ++i) h[i] = carry ? fshr(g[i], g[i + 1], 1) : g[i];
+  xf_pack<W>(h, x.e + (carry ? 1 : 0), x.s, r);
+}
+
+template <int W>
+XF_FN void xf_sub(const xf<W>& a, const xf<W>& b, xf<W>& r) {
+  xf<W> nb = b;
+  xf_neg(nb);
+  xf_add(a, nb, r);
+}
+
+template <int W>
+XF_FN void xf_mul(const xf<W>& a, const xf<W>& b, xf<W>& r) {
+  // columns W-2 .. 2W-1 of the product (column k weighs 2^(64k))
+  uint64_t col[W + 2];
+  uint64_t carry = 0;
+#pragma unroll
+  for (int k = W - 2; k <= 2 * W - 1; ++k) {
+    uint64_t s = carry, c = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const int j = k - i;
+      if (j >= 0 && j < W && k >= W - 2) {
+        const uint64_t lo = a.m[i] * b.m[j];
+        s += lo;
+        c += s < lo;
+      }
+      const int jh = k - 1 - i;
+      if (jh >= 0 && jh < W && k - 1 >= W - 2) {
+        const uint64_t hi = umulhi(a.m[i], b.m[jh]);
+        s += hi;
+        c += s < hi;
+      }
+    }
+    if (k >= W - 2) col[k - (W - 2)] = s;
+    carry = c;
+  }
+  // col[W+1] is the top word; the product of two mantissas in [1, 2) is in
+  // [1, 4): its leading bit is bit 63 or 62 of col[W+1]
+  uint64_t h[W + 1];
+#pragma unroll
+  for (int i = 0; i <= W; ++i) h[i] = col[i + 1];
+  const bool z = xf_is_zero(a) || xf_is_zero(b);
+  if (z) {
+    xf_zero(r);
+    return;
+  }
+  xf_pack<W>(h, a.e + b.e + 1, a.s ^ b.s, r);
+}
+
+template <int W>
+XF_FN void xf_mul_pow2(xf<W>& a, int k) {
+  a.e = xf_is_zero(a) ? XF_ZERO_E : a.e + k;
+}
+
+// ---------------------------------------------------------------------------
+// conversions
+// ---------------------------------------------------------------------------
+template <int W>
+XF_FN void xf_from_double(double x, xf<W>& r) {
+  const uint64_t b = dbits(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const bool z = E == 0;  // zero (subnormals are flushed)
+#pragma unroll
+  for (int i = 0; i < W - 1; ++i) r.m[i] = 0ULL;
+  r.m[W - 1] = z ? 0ULL : (((b & 0xfffffffffffffULL) | 0x10000000000000ULL) << 11);
+  r.e = z ? XF_ZERO_E : E - 1023;
+  r.s = z ? 0 : (int)(b >> 63);
+}
+
+// md -> xf: limb 0 fixes the sign and exponent; each lower limb is added
+// (same sign) or subtracted (opposite sign) at its offset below limb 0 in
+// a fixed-point number of W+2 words (a guard word below the mantissa and a
+// carry word above), which stays positive because limb 0 dominates the sum
+// of the others; one normalisation at the end.
+template <int K, int W>
+XF_FN void xf_from_md(const double (&a)[K], xf<W>& r) {
+  const uint64_t b0 = dbits(a[0]);
+  const int E0 = (int)((b0 >> 52) & 0x7ff);
+  if (E0 == 0) {
+    xf_zero(r);
+    return;
+  }
+  uint64_t g[W + 2];
+#pragma unroll
+  for (int i = 0; i < W; ++i) g[i] = 0ULL;
+  g[W] = ((b0 & 0xfffffffffffffULL) | 0x10000000000000ULL) << 11;
+  g[W + 1] = 0ULL;
+  const uint64_t s0 = b0 >> 63;
+#pragma unroll
+  for (int l = 1; l < K; ++l) {
+    const uint64_t bl = dbits(a[l]);
+    const int El = (int)((bl >> 52) & 0x7ff);
+    uint64_t top[W];
+#pragma unroll
+    for (int i = 0; i < W - 1; ++i) top[i] = 0ULL;
+    top[W - 1] = El == 0 ? 0ULL : (((bl & 0xfffffffffffffULL) | 0x10000000000000ULL) << 11);
+    uint64_t ys[W + 1];
+    shr_guard<W>(top, E0 - El, ys);
+    const uint64_t mask = ((bl >> 63) ^ s0) ? ~0ULL : 0ULL;
+    uint64_t c = mask & 1ULL;
+#pragma unroll
+    for (int i = 0; i <= W; ++i) {
+      const uint64_t yv = ys[i] ^ mask;
+      const uint64_t u = g[i] + yv;
+      const uint64_t c1 = u < g[i];
+      const uint64_t v = u + c;
+      c = c1 | (v < u);
+      g[i] = v;
+    }
+    g[W + 1] += mask + c;
+  }
+  uint64_t h[W + 1];
+  const bool carry = g[W + 1] != 0ULL;
+#pragma unroll
+  for (int i = 0; i <= W; ++i) h[i] = carry ? fshr(g[i], g[i + 1], 1) : g[i];
+  xf_pack<W>(h, E0 - 1023 + (carry ? 1 : 0), (int)s0, r);
+}
+
+// the leading limb: the 53 leading bits rounded to nearest, as a double, and
+// the exact remainder a - limb.
+template <int W>
+XF_FN double xf_take_limb(xf<W>& a) {
+  if (xf_is_zero(a)) return 0.0;
+  const uint64_t top = a.m[W - 1];
+  const uint64_t up = (top >> 10) & 1ULL;
+  uint64_t mant = (top >> 11) + up;
+  int e = a.e;
+  const bool ovf = mant == (1ULL << 53);
+  mant = ovf ? (1ULL << 52) : mant;
+  e += ovf ? 1 : 0;
+  const bool flush = e < -1022;
+  const double limb = flush ? 0.0
+                            : bitsd(((uint64_t)a.s << 63) | ((uint64_t)(e + 1023) << 52) |
+                                    (mant & 0xfffffffffffffULL));
+  if (flush) {
+    xf_zero(a);
+    return 0.0;
+  }
+  // remainder: the bits below the 53 leading ones, minus 2^(64W-53) if
+  // rounded up (then of the opposite sign)
+  uint64_t g[W + 1];
+  g[0] = 0ULL;
+#pragma unroll
+  for (int i = 0; i < W; ++i) g[i + 1] = a.m[i];
+  g[W] &= (1ULL << 11) - 1ULL;
+  if (up) {
+    uint64_t c = 1;
+#pragma unroll
+    for (int i = 0; i <= W; ++i) {
+      const uint64_t v = ~g[i] + c;
+      c = (c != 0ULL && v == 0ULL) ? 1ULL : 0ULL;
+      g[i] = v;
+    }
+    g[W] &= (1ULL << 11) - 1ULL;
+  }
+  xf_pack<W>(g, a.e, up ? a.s ^ 1 : a.s, a);
+  return limb;
+}
+
+template <int K, int W>
+XF_FN void xf_to_md(const xf<W>& a, double (&r)[K]) {
+  xf<W> t = a;
+#pragma unroll
+  for (int l = 0; l < K; ++l) r[l] = xf_take_limb(t);
+}
+
+// the double nearest to the leading 53 bits of a mantissa in [1, 2)
+template <int W>
+XF_FN double xf_mant_double(const xf<W>& a) {
+  const uint64_t top = a.m[W - 1];
+  return bitsd((1023ULL << 52) | ((top >> 11) & 0xfffffffffffffULL));
+}
+
+template <int W>
+struct xf_iters {
+  static constexpr int value = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 3 : 4;
+};
+
+// r = 1 / a, a nonzero
+template <int W>
+XF_FN void xf_recip(const xf<W>& a, xf<W>& r) {
+  xf<W> one, y;
+  xf_from_double(1.0, one);
+  xf_from_double(drecip(xf_mant_double(a)), y);
+  y.e -= a.e;
+  y.s = a.s;
+#pragma unroll 1
+  for (int it = 0; it < xf_iters<W>::value; ++it) {
+    xf<W> t, u;
+    xf_mul(a, y, t);
+    xf_sub(one, t, u);
+    xf_mul(y, u, t);
+    xf_add(y, t, u);
+    y = u;
+  }
+  r = y;
+}
+
+// r = 1 / sqrt(a), a > 0
+template <int W>
+XF_FN void xf_rsqrt(const xf<W>& a, xf<W>& r) {
+  xf<W> one, y;
+  xf_from_double(1.0, one);
+  // a = M 2^e with M in [1, 2); for odd e take 2M 2^(e-1)
+  const bool odd = (a.e & 1) != 0;
+  double md = xf_mant_double(a);
+  md = odd ? md * 2.0 : md;
+  const int eh = (odd ? a.e - 1 : a.e) / 2;
+  xf_from_double(drsqrt(md), y);
+  y.e -= eh;
+#pragma unroll 1
+  for (int it = 0; it < xf_iters<W>::value; ++it) {
+    xf<W> t, u;
+    xf_mul(a, y, t);
+    xf_mul(t, y, u);
+    xf_sub(one, u, t);
+    xf_mul(y, t, u);
+    xf_mul_pow2(u, -1);
+    xf_add(y, u, t);
+    y = t;
+  }
+  r = y;
+}
+
+}  // namespace xfn

@@ -1,0 +1,51 @@
+// Host build of the integer-limb extended floats (xf.cuh) for the CPU tests:
+// md inputs are converted to xf, one operation runs, and the result comes
+// back as an md value of KO limbs (KO = K + 1 shows the xf result itself,
+// below the md precision).
+#include "../../paper_2301_12659_gb300/csrc/xf.cuh"
+
+using namespace xfn;
+
+template <int K, int W, int KO>
+static void run(int op, const double* a, const double* b, double* out) {
+  double la[K], lb[K], r[KO];
+  for (int l = 0; l < K; ++l) {
+    la[l] = a[l];
+    lb[l] = b[l];
+  }
+  xf<W> x, y, z;
+  xf_from_md<K, W>(la, x);
+  xf_from_md<K, W>(lb, y);
+  switch (op) {
+    case 0: z = x; break;
+    case 1: xf_add(x, y, z); break;
+    case 2: xf_sub(x, y, z); break;
+    case 3: xf_mul(x, y, z); break;
+    case 4: xf_recip(x, z); break;
+    case 5: xf_rsqrt(x, z); break;
+    default: xf_zero(z);
+  }
+  xf_to_md<KO, W>(z, r);
+  for (int l = 0; l < KO; ++l) out[l] = r[l];
+}
+
+// op: 0 round trip, 1 add, 2 sub, 3 mul, 4 reciprocal, 5 rsqrt.
+// extra = 0: K output limbs; extra = 1: K + 1 output limbs.
+extern "C" int xf_host_op(int K, int extra, int op, const double* a, const double* b, double* out) {
+  if (extra) {
+    switch (K) {
+      case 1: run<1, 1, 2>(op, a, b, out); return 0;
+      case 2: run<2, 2, 3>(op, a, b, out); return 0;
+      case 4: run<4, 4, 5>(op, a, b, out); return 0;
+      case 8: run<8, 7, 9>(op, a, b, out); return 0;
+    }
+  } else {
+    switch (K) {
+      case 1: run<1, 1, 1>(op, a, b, out); return 0;
+      case 2: run<2, 2, 2>(op, a, b, out); return 0;
+      case 4: run<4, 4, 4>(op, a, b, out); return 0;
+      case 8: run<8, 7, 8>(op, a, b, out); return 0;
+    }
+  }
+  return 1;
+}

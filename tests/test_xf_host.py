@@ -1,0 +1,156 @@
+"""The integer-limb extended floats (csrc/xf.cuh), compiled for the host and
+checked against exact rationals: conversions from and to multiple doubles,
+add, sub, mul, reciprocal and reciprocal square root, zero and cancellation.
+
+An xf of W 64-bit words carries 64W bits; each operation must be correct to
+a few units of 2^(-64W) (far below the 2^(-53K) of the K-limb md values it
+serves), and its md output must be K nonoverlapping limbs rounded to
+nearest."""
+import ctypes
+import math
+import os
+import subprocess
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+from paper_2301_12659_gb300 import workloads as wl
+from tests import exact as ex
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+WORDS = {1: 1, 2: 2, 4: 4, 8: 7}
+OPS = {"copy": 0, "add": 1, "sub": 2, "mul": 3, "recip": 4, "rsqrt": 5}
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    so = str(tmp_path_factory.mktemp("xf") / "xf_host.so")
+    src = os.path.join(HERE, "native", "xf_host.cpp")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", so, src], check=True)
+    h = ctypes.CDLL(so)
+    h.xf_host_op.restype = ctypes.c_int
+    return h
+
+
+def _op(lib, K, op, a, b=None, extra=False):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(a if b is None else b, dtype=np.float64)
+    out = np.zeros(K + (1 if extra else 0))
+    p = ctypes.POINTER(ctypes.c_double)
+    rc = lib.xf_host_op(K, int(extra), OPS[op], a.ctypes.data_as(p), b.ctypes.data_as(p), out.ctypes.data_as(p))
+    assert rc == 0
+    return out
+
+
+def _values(K, count, seed, spread=40):
+    """md values [count][K] of full width with magnitudes 2^-spread..2^spread."""
+    v = wl.random_md((count,), K, 1, seed)[:, 0].T.copy()
+    rng = np.random.default_rng(seed)
+    v *= np.exp2(rng.integers(-spread, spread + 1, size=count))[:, None]
+    return v
+
+
+def _nonoverlapping(limbs):
+    for l in range(len(limbs) - 1):
+        if limbs[l] == 0.0:
+            assert np.all(np.asarray(limbs[l:]) == 0.0)
+            return
+        assert abs(limbs[l + 1]) <= np.spacing(abs(limbs[l])) / 2
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+def test_round_trip(lib, K):
+    """md -> xf -> md is exact when the limbs span at most 64W bits (most
+    values: the limbs of a full-width value lie 53 bits apart, with a gap
+    where a limb is small) and otherwise loses only bits below 2^(1-64W)."""
+    W = WORDS[K]
+    exact = 0
+    for a in _values(K, 200, 900 + K):
+        out = _op(lib, K, "copy", a)
+        A = ex.md_to_fr(a)
+        assert abs(ex.md_to_fr(out) - A) <= Fr(2) ** (1 - 64 * W) * abs(A)
+        _nonoverlapping(out)
+        exact += ex.md_to_fr(out) == A
+    assert exact >= 150
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+@pytest.mark.parametrize("op", ["add", "sub", "mul"])
+def test_arithmetic_to_xf_precision(lib, K, op):
+    W = WORDS[K]
+    va, vb = _values(K, 150, 910 + K), _values(K, 150, 920 + K, spread=3)
+    for a, b in zip(va, vb):
+        A, B = ex.md_to_fr(a), ex.md_to_fr(b)
+        want = A + B if op == "add" else A - B if op == "sub" else A * B
+        got = _op(lib, K, op, a, b, extra=True)
+        _nonoverlapping(got)
+        err = abs(ex.md_to_fr(got) - want)
+        bound = Fr(2) ** (3 - 64 * W) * abs(want)
+        if op != "mul":
+            bound += Fr(2) ** (-64 * W - 60) * max(abs(A), abs(B))
+        assert err <= bound, (op, float(err), float(want))
+        # rounded to K limbs: nearest, to the md precision
+        gk = _op(lib, K, op, a, b)
+        _nonoverlapping(gk)
+        assert abs(ex.md_to_fr(gk) - want) <= Fr(2) ** (1 - 53 * K) * abs(want) + bound
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+def test_cancellation_is_exact(lib, K):
+    """a - b for b a few units of the last limb away from a: the difference
+    is formed exactly (the guard word), whatever the exponents."""
+    rng = np.random.default_rng(930 + K)
+    for a in _values(K, 60, 931 + K):
+        A = ex.md_to_fr(a)
+        tiny = Fr(int(rng.integers(-9, 10))) * Fr(2) ** (math.frexp(a[0])[1] - 53 * K - 3)
+        b = np.array(ex.fr_to_md(A + tiny, K))
+        if ex.md_to_fr(b) == A:
+            continue
+        got = _op(lib, K, "sub", a, b, extra=True)
+        assert ex.md_to_fr(got) == A - ex.md_to_fr(b)
+    one = np.zeros(K)
+    one[0] = 1.0
+    below = np.zeros(K)
+    below[0] = 1.0 - 2.0 ** -53
+    got = _op(lib, K, "sub", one, below, extra=True)
+    assert ex.md_to_fr(got) == Fr(2) ** -53
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+def test_zero(lib, K):
+    z = np.zeros(K)
+    a = _values(K, 1, 940 + K)[0]
+    assert ex.md_to_fr(_op(lib, K, "add", z, a)) == ex.md_to_fr(a)
+    assert ex.md_to_fr(_op(lib, K, "add", a, z)) == ex.md_to_fr(a)
+    assert np.all(_op(lib, K, "mul", z, a) == 0.0)
+    assert np.all(_op(lib, K, "sub", a, a) == 0.0)
+    assert np.all(_op(lib, K, "add", z, z) == 0.0)
+    na = -a
+    assert np.all(_op(lib, K, "add", a, na) == 0.0)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+def test_reciprocal_and_rsqrt(lib, K):
+    W = WORDS[K]
+    tol = Fr(2) ** (8 - 64 * W)
+    for a in _values(K, 100, 950 + K, spread=60):
+        A = ex.md_to_fr(a)
+        y = ex.md_to_fr(_op(lib, K, "recip", a, extra=True))
+        assert abs(y * A - 1) <= tol
+        yk = _op(lib, K, "recip", a)
+        _nonoverlapping(yk)
+        assert abs(ex.md_to_fr(yk) * A - 1) <= Fr(2) ** (2 - 53 * K)
+        if a[0] < 0:  # a positive value
+            a, A = -a, -A
+        r = ex.md_to_fr(_op(lib, K, "rsqrt", a, extra=True))
+        assert abs(r * r * A - 1) <= tol
+        rk = _op(lib, K, "rsqrt", a)
+        assert abs(ex.md_to_fr(rk) ** 2 * A - 1) <= Fr(2) ** (3 - 53 * K)
+    # exact cases
+    for v, r in ((1.0, 1), (4.0, Fr(1, 2)), (0.25, 2), (2.0 ** 40, Fr(1, 2 ** 20)), (2.0 ** -42, 2 ** 21)):
+        a = np.zeros(K)
+        a[0] = v
+        assert ex.md_to_fr(_op(lib, K, "rsqrt", a)) == r
+        assert ex.md_to_fr(_op(lib, K, "recip", a)) == 1 / Fr(v)
+        assert ex.md_to_fr(_op(lib, K, "recip", -a)) == -1 / Fr(v)

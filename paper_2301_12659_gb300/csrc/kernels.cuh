@@ -249,8 +249,102 @@ __device__ __forceinline__ void series_product(const SP& a, const SP& b, const S
   if (k2 != k1) st(o.p, o.N, o.off + k2, r2);
 }
 
+// The same product in integer-limb extended floats (xf.cuh), for K >= 2:
+// the group's lanes convert the D coefficients of a and b once into the
+// group's shared memory; lane t then sums the t+1 products of coefficient
+// k1 = t and the D-t products of coefficient k2 = D-1-t in fixed-point
+// accumulators (one per coefficient, real and imaginary part), their scale
+// set beforehand from the largest exponent sum of their terms, so a term is
+// an integer product, a shift and an add on the integer pipe.  Each result
+// is rounded to K limbs once.
+template <int K, int C>
+__device__ __forceinline__ void series_product_xf(const SP& a, const SP& b, const SP& o, int t, int D,
+                                                  unsigned gmask, xfn::xf<xfn::xf_words_t<K>::value>* stage) {
+  using namespace xfn;
+  constexpr int W = xf_words_t<K>::value;
+  xf<W>* sa = stage;          // [C][D]
+  xf<W>* sb = stage + C * D;  // [C][D]
+  const int k1 = t, k2 = D - 1 - t;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int k = q ? k2 : k1;
+    if (q == 1 && k2 == k1) break;
+    cmd<K, C> v;
+    ld(a.p, a.N, a.off + k, v);
+    xf_from_md<K, W>(v.re, sa[k]);
+    if constexpr (C == 2) xf_from_md<K, W>(v.im, sa[D + k]);
+    ld(b.p, b.N, b.off + k, v);
+    xf_from_md<K, W>(v.re, sb[k]);
+    if constexpr (C == 2) xf_from_md<K, W>(v.im, sb[D + k]);
+  }
+  __syncwarp(gmask);
+  // term s = 0..D: coefficient k1 for s <= k1 (i = s), then k2 (i = s-k1-1)
+  int e1r = 2 * XF_ZERO_E, e2r = 2 * XF_ZERO_E, e1i = 2 * XF_ZERO_E, e2i = 2 * XF_ZERO_E;
+  for (int s = 0; s <= D; ++s) {
+    const bool first = s <= k1;
+    const int i = first ? s : s - k1 - 1;
+    const int j = (first ? k1 : k2) - i;
+    int er = sa[i].e + sb[j].e, ei = er;
+    if constexpr (C == 2) {
+      const int ar = sa[i].e, ai = sa[D + i].e, br = sb[j].e, bi = sb[D + j].e;
+      er = max(ar + br, ai + bi);
+      ei = max(ar + bi, ai + br);
+    }
+    if (first) {
+      e1r = max(e1r, er);
+      e1i = max(e1i, ei);
+    } else {
+      e2r = max(e2r, er);
+      e2i = max(e2i, ei);
+    }
+  }
+  xfacc<W> cr, ci, dr, di;
+  xfacc_init(cr, e1r);
+  if constexpr (C == 2) xfacc_init(ci, e1i);
+  for (int s = 0; s <= D; ++s) {
+    if (s == k1 + 1) {
+      dr = cr;
+      xfacc_init(cr, e2r);
+      if constexpr (C == 2) {
+        di = ci;
+        xfacc_init(ci, e2i);
+      }
+    }
+    const bool first = s <= k1;
+    const int i = first ? s : s - k1 - 1;
+    const int j = (first ? k1 : k2) - i;
+    const xf<W> ar = sa[i], br = sb[j];
+    xfacc_fma(cr, ar, br);
+    if constexpr (C == 2) {
+      const xf<W> ai = sa[D + i], bi = sb[D + j];
+      xfacc_fma(cr, ai, bi, true);
+      xfacc_fma(ci, ar, bi);
+      xfacc_fma(ci, ai, br);
+    }
+  }
+  cmd<K, C> r;
+  xf<W> x;
+  xfacc_get(dr, x);
+  xf_to_md<K, W>(x, r.re);
+  if constexpr (C == 2) {
+    xfacc_get(di, x);
+    xf_to_md<K, W>(x, r.im);
+  }
+  st(o.p, o.N, o.off + k1, r);
+  if (k2 != k1) {
+    xfacc_get(cr, x);
+    xf_to_md<K, W>(x, r.re);
+    if constexpr (C == 2) {
+      xfacc_get(ci, x);
+      xf_to_md<K, W>(x, r.im);
+    }
+    st(o.p, o.N, o.off + k2, r);
+  }
+}
+
 template <int K, int C>
 __global__ void __launch_bounds__(ED_THREADS) ed_kernel(EdParams p) {
+  extern __shared__ __align__(16) unsigned char ed_smem[];
   const int lane = threadIdx.x & 31;
   const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int g = lane / p.P, t = lane - g * p.P;
@@ -268,7 +362,16 @@ __global__ void __launch_bounds__(ED_THREADS) ed_kernel(EdParams p) {
     for (int w = 0; w < nw; ++w) {
       const int4 op = ingroup ? sc[w * p.G + g] : make_int4(0, 0, 0, 0);
       if (op.x == OP_PRODUCT) {
-        series_product<K, C>(resolve(p, op.z, m, wg), resolve(p, op.w, m, wg), resolve(p, op.y, m, wg), t, p.len);
+        if constexpr (K >= 2) {
+          // shared memory: per warp G groups of 2 C len xf values (G len <= 64)
+          using X = xfn::xf<xfn::xf_words_t<K>::value>;
+          X* stage = reinterpret_cast<X*>(ed_smem) + ((threadIdx.x >> 5) * p.G + g) * (2 * C * p.len);
+          const unsigned gmask = (p.P >= 32 ? FULL : ((1u << p.P) - 1u)) << (g * p.P);
+          series_product_xf<K, C>(resolve(p, op.z, m, wg), resolve(p, op.w, m, wg), resolve(p, op.y, m, wg), t,
+                                  p.len, gmask, stage);
+        } else {
+          series_product<K, C>(resolve(p, op.z, m, wg), resolve(p, op.w, m, wg), resolve(p, op.y, m, wg), t, p.len);
+        }
       } else if (op.x == OP_COPY) {
         const SP s = resolve(p, op.z, m, wg), d = resolve(p, op.y, m, wg);
         cmd<K, C> v;

@@ -24,7 +24,8 @@
 //   * reciprocal and reciprocal square root: Newton's iterations for 1/a
 //     and 1/sqrt(a) (y += y(1 - ay), y += y(1 - ay^2)/2), started from the
 //     double precision reciprocal / reciprocal square root of the leading
-//     53 bits and repeated until 53 * 2^iterations >= 64W;
+//     53 bits, each step at the narrowest width that holds the bits it
+//     makes correct, until all 64W bits are;
 //   * xf -> md: K times, the leading 53 bits rounded to nearest give a limb
 //     and the exact remainder goes on, so the limbs are nonoverlapping with
 //     |limb_{l+1}| <= ulp(limb_l)/2.
@@ -275,10 +276,12 @@ XF_FN void xf_sub(const xf<W>& a, const xf<W>& b, xf<W>& r) {
   xf_add(a, nb, r);
 }
 
+// The top W+1 words of the product of the mantissas of a and b, worth
+// H / 2^(64W+63) * 2^(a.e + b.e + 1): the columns W-2 .. 2W-1 of the
+// 2W-word product (column k weighs 2^(64k)); the products landing below
+// column W-2 are dropped.
 template <int W>
-XF_FN void xf_mul(const xf<W>& a, const xf<W>& b, xf<W>& r) {
-  // columns W-2 .. 2W-1 of the product (column k weighs 2^(64k))
-  uint64_t col[W + 2];
+XF_FN void xf_mul_core(const xf<W>& a, const xf<W>& b, uint64_t (&h)[W + 1]) {
   uint64_t carry = 0;
 #pragma unroll
   for (int k = W - 2; k <= 2 * W - 1; ++k) {
@@ -286,7 +289,7 @@ XF_FN void xf_mul(const xf<W>& a, const xf<W>& b, xf<W>& r) {
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       const int j = k - i;
-      if (j >= 0 && j < W && k >= W - 2) {
+      if (j >= 0 && j < W) {
         const uint64_t lo = a.m[i] * b.m[j];
         s += lo;
         c += s < lo;
@@ -298,20 +301,116 @@ XF_FN void xf_mul(const xf<W>& a, const xf<W>& b, xf<W>& r) {
         c += s < hi;
       }
     }
-    if (k >= W - 2) col[k - (W - 2)] = s;
+    if (k >= W - 1) h[k - (W - 1)] = s;
     carry = c;
   }
-  // col[W+1] is the top word; the product of two mantissas in [1, 2) is in
-  // [1, 4): its leading bit is bit 63 or 62 of col[W+1]
+}
+
+template <int W>
+XF_FN void xf_mul(const xf<W>& a, const xf<W>& b, xf<W>& r) {
+  // the product of two mantissas in [1, 2) is in [1, 4): its leading bit is
+  // bit 63 or 62 of the top word
   uint64_t h[W + 1];
-#pragma unroll
-  for (int i = 0; i <= W; ++i) h[i] = col[i + 1];
+  xf_mul_core(a, b, h);
   const bool z = xf_is_zero(a) || xf_is_zero(b);
   if (z) {
     xf_zero(r);
     return;
   }
   xf_pack<W>(h, a.e + b.e + 1, a.s ^ b.s, r);
+}
+
+// r = a >> s for s >= 0 (N words, truncated; s >= 64N gives zero)
+template <int N>
+XF_FN void shr_words(const uint64_t (&a)[N], int s, uint64_t (&r)[N]) {
+  const int q = s >> 6;
+  const int b = s & 63;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r[i] = a[i];
+#pragma unroll
+  for (int st = 1; st < N; st <<= 1) {
+    const bool on = (q & st) != 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r[i] = on ? (i + st < N ? r[i + st] : 0ULL) : r[i];
+  }
+  const bool gone = q >= N;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const uint64_t v = fshr(r[i], i + 1 < N ? r[i + 1] : 0ULL, b);
+    r[i] = gone ? 0ULL : v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fixed-point accumulation of products (dot products, convolutions)
+// ---------------------------------------------------------------------------
+// A sum of up to XF_ACC_TERMS products a_i b_i in a two's complement integer
+// T of W+2 words, worth T / 2^(64W+63) * 2^E.  E is fixed before the first
+// product from the largest exponent sum e_max = max(a_i.e + b_i.e):
+// E = e_max + 1 + XF_ACC_HEAD, so every product (< 2^(e_max+2)) enters with
+// a right shift of at least XF_ACC_HEAD bits and the sum cannot overflow.
+// The sum is exact but for the bits shifted out below the W+1 words, so its
+// error is below (terms) 2^(XF_ACC_HEAD+1-64(W+1)) times the largest term:
+// the accuracy of an md dot product (error relative to the sum of
+// magnitudes), with 64 - XF_ACC_HEAD bits to spare.
+constexpr int XF_ACC_HEAD = 9;
+constexpr int XF_ACC_TERMS = 1 << (XF_ACC_HEAD - 1);
+
+template <int W>
+struct xfacc {
+  uint64_t w[W + 2];
+  int E;
+};
+
+template <int W>
+XF_FN void xfacc_init(xfacc<W>& a, int e_max) {
+#pragma unroll
+  for (int i = 0; i < W + 2; ++i) a.w[i] = 0ULL;
+  a.E = e_max + 1 + XF_ACC_HEAD;
+}
+
+// the exponent sum that xfacc_init wants for the product x y (very negative
+// when either is zero)
+template <int W>
+XF_FN int xf_prod_exp(const xf<W>& x, const xf<W>& y) {
+  return x.e + y.e;
+}
+
+// a += x y (neg: a -= x y)
+template <int W>
+XF_FN void xfacc_fma(xfacc<W>& a, const xf<W>& x, const xf<W>& y, bool neg = false) {
+  uint64_t h[W + 1], r[W + 1];
+  xf_mul_core(x, y, h);
+  const bool z = xf_is_zero(x) || xf_is_zero(y);
+  const int d = a.E - (x.e + y.e + 1);
+  shr_words<W + 1>(h, z ? 64 * (W + 1) : d, r);
+  const uint64_t mask = ((x.s ^ y.s) != 0) != neg ? ~0ULL : 0ULL;
+  uint64_t c = mask & 1ULL;
+#pragma unroll
+  for (int i = 0; i <= W; ++i) {
+    const uint64_t yv = r[i] ^ mask;
+    const uint64_t u = a.w[i] + yv;
+    const uint64_t c1 = u < a.w[i];
+    const uint64_t v = u + c;
+    c = c1 | (v < u);
+    a.w[i] = v;
+  }
+  a.w[W + 1] += mask + c;
+}
+
+template <int W>
+XF_FN void xfacc_get(const xfacc<W>& a, xf<W>& r) {
+  const bool neg = (a.w[W + 1] >> 63) != 0ULL;
+  uint64_t g[W + 1];
+  uint64_t c = neg ? 1ULL : 0ULL;
+  const uint64_t mask = neg ? ~0ULL : 0ULL;
+#pragma unroll
+  for (int i = 0; i <= W; ++i) {
+    const uint64_t v = (a.w[i] ^ mask) + c;
+    c = (c != 0ULL && v == 0ULL) ? 1ULL : 0ULL;
+    g[i] = v;
+  }
+  xf_pack<W>(g, a.E, neg ? 1 : 0, r);
 }
 
 template <int W>
@@ -438,36 +537,87 @@ XF_FN double xf_mant_double(const xf<W>& a) {
   return bitsd((1023ULL << 52) | ((top >> 11) & 0xfffffffffffffULL));
 }
 
-template <int W>
-struct xf_iters {
-  static constexpr int value = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 3 : 4;
-};
+// a at another width: the leading min(W1, W2) words, zero extended
+template <int W2, int W1>
+XF_FN void xf_resize(const xf<W1>& a, xf<W2>& r) {
+#pragma unroll
+  for (int i = 0; i < W2; ++i) r.m[W2 - 1 - i] = i < W1 ? a.m[W1 - 1 - i] : 0ULL;
+  r.e = a.e;
+  r.s = a.s;
+}
+
+// one Newton step for 1/a at width V: y += y (1 - a y)
+template <int V>
+XF_FN void recip_step(const xf<V>& a, xf<V>& y) {
+  xf<V> one, t, u;
+  xf_from_double(1.0, one);
+  xf_mul(a, y, t);
+  xf_sub(one, t, u);
+  xf_mul(y, u, t);
+  xf_add(y, t, u);
+  y = u;
+}
+// one Newton step for 1/sqrt(a) at width V: y += y (1 - a y^2) / 2
+template <int V>
+XF_FN void rsqrt_step(const xf<V>& a, xf<V>& y) {
+  xf<V> one, t, u;
+  xf_from_double(1.0, one);
+  xf_mul(a, y, t);
+  xf_mul(t, y, u);
+  xf_sub(one, u, t);
+  xf_mul(y, t, u);
+  xf_mul_pow2(u, -1);
+  xf_add(y, u, t);
+  y = t;
+}
+// the step at width V on the W-word a and y
+template <int V, bool RSQRT, int W>
+XF_FN void newton_at(const xf<W>& a, xf<W>& y) {
+  xf<V> av, yv;
+  xf_resize<V>(a, av);
+  xf_resize<V>(y, yv);
+  if constexpr (RSQRT) rsqrt_step<V>(av, yv);
+  else recip_step<V>(av, yv);
+  xf_resize<W>(yv, y);
+}
+// From a 53-bit seed each step doubles the correct bits up to the width it
+// runs at, so the early steps run narrower: widths 1; 1, 2; 2, 4, 4;
+// 2, 4, 7, 7 for W = 1, 2, 4, 7 (53 -> 64; 64 -> 128; 106 -> 212 -> 256;
+// 106 -> 212 -> 424 -> 448 bits).
+template <bool RSQRT, int W>
+XF_FN void newton_steps(const xf<W>& a, xf<W>& y) {
+  if constexpr (W == 1) {
+    newton_at<1, RSQRT>(a, y);
+  } else if constexpr (W == 2) {
+    newton_at<1, RSQRT>(a, y);
+    newton_at<2, RSQRT>(a, y);
+  } else if constexpr (W <= 4) {
+    newton_at<2, RSQRT>(a, y);
+    newton_at<W, RSQRT>(a, y);
+    newton_at<W, RSQRT>(a, y);
+  } else {
+    newton_at<2, RSQRT>(a, y);
+    newton_at<4, RSQRT>(a, y);
+    newton_at<W, RSQRT>(a, y);
+    newton_at<W, RSQRT>(a, y);
+  }
+}
 
 // r = 1 / a, a nonzero
 template <int W>
 XF_FN void xf_recip(const xf<W>& a, xf<W>& r) {
-  xf<W> one, y;
-  xf_from_double(1.0, one);
+  xf<W> y;
   xf_from_double(drecip(xf_mant_double(a)), y);
   y.e -= a.e;
   y.s = a.s;
-#pragma unroll 1
-  for (int it = 0; it < xf_iters<W>::value; ++it) {
-    xf<W> t, u;
-    xf_mul(a, y, t);
-    xf_sub(one, t, u);
-    xf_mul(y, u, t);
-    xf_add(y, t, u);
-    y = u;
-  }
+  newton_steps<false>(a, y);
   r = y;
 }
 
 // r = 1 / sqrt(a), a > 0
 template <int W>
 XF_FN void xf_rsqrt(const xf<W>& a, xf<W>& r) {
-  xf<W> one, y;
-  xf_from_double(1.0, one);
+  xf<W> y;
   // a = M 2^e with M in [1, 2); for odd e take 2M 2^(e-1)
   const bool odd = (a.e & 1) != 0;
   double md = xf_mant_double(a);
@@ -475,17 +625,7 @@ XF_FN void xf_rsqrt(const xf<W>& a, xf<W>& r) {
   const int eh = (odd ? a.e - 1 : a.e) / 2;
   xf_from_double(drsqrt(md), y);
   y.e -= eh;
-#pragma unroll 1
-  for (int it = 0; it < xf_iters<W>::value; ++it) {
-    xf<W> t, u;
-    xf_mul(a, y, t);
-    xf_mul(t, y, u);
-    xf_sub(one, u, t);
-    xf_mul(y, t, u);
-    xf_mul_pow2(u, -1);
-    xf_add(y, u, t);
-    y = t;
-  }
+  newton_steps<true>(a, y);
   r = y;
 }
 

@@ -49,3 +49,47 @@ extern "C" int xf_host_op(int K, int extra, int op, const double* a, const doubl
   }
   return 1;
 }
+
+// c = a * b mod t^D for md series a, b ([D][K] limbs each) with one
+// fixed-point accumulator per coefficient; c as [D][KO] limbs.
+template <int K, int W, int KO>
+static void conv(int D, const double* a, const double* b, double* out) {
+  xf<W> xa[64], xb[64];
+  for (int i = 0; i < D; ++i) {
+    double la[K], lb[K];
+    for (int l = 0; l < K; ++l) {
+      la[l] = a[i * K + l];
+      lb[l] = b[i * K + l];
+    }
+    xf_from_md<K, W>(la, xa[i]);
+    xf_from_md<K, W>(lb, xb[i]);
+  }
+  for (int k = 0; k < D; ++k) {
+    int e = XF_ZERO_E * 2;
+    for (int i = 0; i <= k; ++i) {
+      const int ei = xf_prod_exp(xa[i], xb[k - i]);
+      e = ei > e ? ei : e;
+    }
+    xfacc<W> acc;
+    xfacc_init(acc, e);
+    for (int i = 0; i <= k; ++i) xfacc_fma(acc, xa[i], xb[k - i], (i & 1) != 0 && k == D - 1);
+    xf<W> r;
+    xfacc_get(acc, r);
+    double o[KO];
+    xf_to_md<KO, W>(r, o);
+    for (int l = 0; l < KO; ++l) out[k * KO + l] = o[l];
+  }
+}
+
+// The last coefficient alternates the signs of its terms (exercises the
+// subtracting path of the accumulator).
+extern "C" int xf_host_conv(int K, int D, const double* a, const double* b, double* out) {
+  if (D < 1 || D > 64) return 1;
+  switch (K) {
+    case 1: conv<1, 1, 2>(D, a, b, out); return 0;
+    case 2: conv<2, 2, 3>(D, a, b, out); return 0;
+    case 4: conv<4, 4, 5>(D, a, b, out); return 0;
+    case 8: conv<8, 7, 9>(D, a, b, out); return 0;
+  }
+  return 1;
+}

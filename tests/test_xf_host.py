@@ -154,3 +154,32 @@ def test_reciprocal_and_rsqrt(lib, K):
         assert ex.md_to_fr(_op(lib, K, "rsqrt", a)) == r
         assert ex.md_to_fr(_op(lib, K, "recip", a)) == 1 / Fr(v)
         assert ex.md_to_fr(_op(lib, K, "recip", -a)) == -1 / Fr(v)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+@pytest.mark.parametrize("D", [1, 7, 32, 64])
+def test_fixed_point_convolution(lib, K, D):
+    """c = a b mod t^D, one fixed-point accumulator per coefficient: error
+    below 2^(12-64W) times the sum of the magnitudes of its terms (the md
+    dot-product bound, with the accumulator's headroom), the last
+    coefficient with alternating signs.  Coefficients of both series span
+    2^-30..2^30 and include exact zeros."""
+    W = WORDS[K]
+    a = _values(K, D, 960 + K + D, spread=30)
+    b = _values(K, D, 970 + K + D, spread=30)
+    if D > 3:
+        a[2] = 0.0
+        b[D - 2] = 0.0
+    out = np.zeros((D, K + 1))
+    p = ctypes.POINTER(ctypes.c_double)
+    ac, bc = np.ascontiguousarray(a), np.ascontiguousarray(b)
+    assert lib.xf_host_conv(K, D, ac.ctypes.data_as(p), bc.ctypes.data_as(p), out.ctypes.data_as(p)) == 0
+    A = [ex.md_to_fr(v) for v in a]
+    B = [ex.md_to_fr(v) for v in b]
+    for k in range(D):
+        terms = [A[i] * B[k - i] * (-1 if (i % 2 and k == D - 1) else 1) for i in range(k + 1)]
+        want = sum(terms, Fr(0))
+        mag = sum((abs(t) for t in terms), Fr(0))
+        got = ex.md_to_fr(out[k])
+        _nonoverlapping(out[k])
+        assert abs(got - want) <= Fr(2) ** (12 - 64 * W) * mag, (k, float(got - want), float(mag))

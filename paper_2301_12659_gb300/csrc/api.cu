@@ -401,8 +401,8 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_adj = take(8 * KC * (size_t)ctx->Wtot * 2 * ctx->G * D);  // products of the adjoint
   L.o_A = take(8 * KC * D * n * n);
   L.o_A0b = take(8 * KC * n * n * 2);  // A_0 of this step and of the next (pipelined QR)
-  L.o_Rm = take(8 * KC * n * n);
-  L.o_Vm = take(8 * KC * n * n);
+  L.o_Rm = take(8 * (size_t)qr_xf_words(ctx->K) * ctx->C * n * n);  // extended floats
+  L.o_Vm = take(8 * (size_t)qr_xf_words(ctx->K) * ctx->C * n * n);
   L.o_Y = take(8 * KC * n * n);
   L.o_Z = take(8 * KC * n * n);
   L.o_W = take(8 * KC * n * n * 2);    // A_0^{-1} of this step and of the next
@@ -657,8 +657,8 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* 
   q.A0 = A0;
   q.NA = NA0;
   q.Nnn = n * n;
-  q.Rm = ctx->at<double>(L.o_Rm);
-  q.Vm = ctx->at<double>(L.o_Vm);
+  q.Rm = ctx->at<uint64_t>(L.o_Rm);
+  q.Vm = ctx->at<uint64_t>(L.o_Vm);
   q.Y = ctx->at<double>(L.o_Y);
   q.Z = ctx->at<double>(L.o_Z);
   q.W = W;

@@ -582,87 +582,171 @@ __device__ __forceinline__ void cxf_scale(const cxf<W, C>& a, const xfn::xf<W>& 
   if constexpr (C == 2) xfn::xf_mul(a.im, s, r.im);
   else xfn::xf_zero(r.im);
 }
-template <int W>
-__device__ __forceinline__ void xf_shfl_xor(const xfn::xf<W>& a, xfn::xf<W>& o, int off) {
-#pragma unroll
-  for (int i = 0; i < W; ++i) o.m[i] = __shfl_xor_sync(FULL, a.m[i], off);
-  o.e = __shfl_xor_sync(FULL, a.e, off);
-  o.s = __shfl_xor_sync(FULL, a.s, off);
-}
-template <int W>
-__device__ __forceinline__ void xf_bcast(xfn::xf<W>& a, int src) {
-#pragma unroll
-  for (int i = 0; i < W; ++i) a.m[i] = __shfl_sync(FULL, a.m[i], src);
-  a.e = __shfl_sync(FULL, a.e, src);
-  a.s = __shfl_sync(FULL, a.s, src);
-}
-// sum over the warp; every lane gets lane 0's total
+// extended floats as the QR stores them: [W+1][C][N] 64-bit words, the W
+// mantissa words and one word holding the exponent (low half) and sign
 template <int W, int C>
-__device__ __forceinline__ void cxf_warp_sum(cxf<W, C>& v) {
+__device__ __forceinline__ void xld(const uint64_t* p, long long N, long long i, cxf<W, C>& v) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    v.re.m[w] = p[(long long)(w * C) * N + i];
+    if constexpr (C == 2) v.im.m[w] = p[(long long)(w * C + 1) * N + i];
+  }
+  const uint64_t h = p[(long long)(W * C) * N + i];
+  v.re.e = (int)(unsigned)h;
+  v.re.s = (int)(h >> 32);
+  if constexpr (C == 2) {
+    const uint64_t g = p[(long long)(W * C + 1) * N + i];
+    v.im.e = (int)(unsigned)g;
+    v.im.s = (int)(g >> 32);
+  } else {
+    xfn::xf_zero(v.im);
+  }
+}
+template <int W, int C>
+__device__ __forceinline__ void xst(uint64_t* p, long long N, long long i, const cxf<W, C>& v) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    p[(long long)(w * C) * N + i] = v.re.m[w];
+    if constexpr (C == 2) p[(long long)(w * C + 1) * N + i] = v.im.m[w];
+  }
+  p[(long long)(W * C) * N + i] = (uint64_t)(unsigned)v.re.e | ((uint64_t)(unsigned)v.re.s << 32);
+  if constexpr (C == 2)
+    p[(long long)(W * C + 1) * N + i] = (uint64_t)(unsigned)v.im.e | ((uint64_t)(unsigned)v.im.s << 32);
+}
+// the exponents alone (for the scale of a fixed-point sum)
+template <int W, int C>
+__device__ __forceinline__ void xld_exp(const uint64_t* p, long long N, long long i, int& er, int& ei) {
+  er = (int)(unsigned)p[(long long)(W * C) * N + i];
+  ei = C == 2 ? (int)(unsigned)p[(long long)(W * C + 1) * N + i] : 2 * xfn::XF_ZERO_E;
+}
+template <int W, int C>
+__device__ __forceinline__ void xcopy(const uint64_t* src, long long Ns, long long is, uint64_t* dst, long long Nd,
+                                      long long id) {
+#pragma unroll
+  for (int w = 0; w < (W + 1) * C; ++w) dst[(long long)w * Nd + id] = src[(long long)w * Ns + is];
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(FULL, v, off));
+  return v;
+}
+// sum over the warp of fixed-point accumulators of one scale
+template <int W>
+__device__ __forceinline__ void xfacc_warp_sum(xfn::xfacc<W>& a) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    cxf<W, C> o;
-    xf_shfl_xor(v.re, o.re, off);
-    xfn::xf_add(v.re, o.re, v.re);
-    if constexpr (C == 2) {
-      xf_shfl_xor(v.im, o.im, off);
-      xfn::xf_add(v.im, o.im, v.im);
+    uint64_t o[W + 2];
+#pragma unroll
+    for (int i = 0; i < W + 2; ++i) o[i] = __shfl_xor_sync(FULL, a.w[i], off);
+    uint64_t c = 0;
+#pragma unroll
+    for (int i = 0; i < W + 2; ++i) {
+      const uint64_t u = a.w[i] + o[i];
+      const uint64_t c1 = u < o[i];
+      const uint64_t v = u + c;
+      c = c1 | (v < u);
+      a.w[i] = v;
     }
   }
-  xf_bcast(v.re, 0);
-  if constexpr (C == 2) xf_bcast(v.im, 0);
+}
+
+// Fixed-point dot product over the warp: sum of conj(x_i) y_i (conj_x) or
+// x_i y_i for the rows the lanes pass in; the scale comes from a first
+// pass over the exponents (a warp maximum), so every lane accumulates at the
+// same scale and the warp sum is an integer sum.
+template <bool conj_x, int W, int C>
+__device__ __forceinline__ void dot_exp(int xr, int xi, int yr, int yi, int& er, int& ei) {
+  er = max(er, max(xr + yr, xi + yi));
+  ei = max(ei, max(xr + yi, xi + yr));
+}
+template <bool conj_x, int W, int C>
+__device__ __forceinline__ void dot_fma(xfn::xfacc<W>& ar, xfn::xfacc<W>& ai, const cxf<W, C>& x, const cxf<W, C>& y) {
+  xfn::xfacc_fma(ar, x.re, y.re);
+  if constexpr (C == 2) {
+    // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr);  x y = (xr yr - xi yi) + i (xr yi + xi yr)
+    xfn::xfacc_fma(ar, x.im, y.im, !conj_x);
+    xfn::xfacc_fma(ai, x.re, y.im);
+    xfn::xfacc_fma(ai, x.im, y.re, conj_x);
+  }
+}
+template <int W, int C>
+__device__ __forceinline__ void dot_finish(xfn::xfacc<W>& ar, xfn::xfacc<W>& ai, cxf<W, C>& r) {
+  xfacc_warp_sum(ar);
+  xfn::xfacc_get(ar, r.re);
+  if constexpr (C == 2) {
+    xfacc_warp_sum(ai);
+    xfn::xfacc_get(ai, r.im);
+  } else {
+    xfn::xf_zero(r.im);
+  }
 }
 
 // dot = sum of conj(x_j[i]) y[i] over rows i = j..n-1 (x_j from Vm).
 template <int K, int C>
-__device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const double* y,
+__device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const uint64_t* y,
                                              cxf<xfn::xf_words_t<K>::value, C>& dot) {
   constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
-  cxf_zero(dot);
+  int er = 2 * xfn::XF_ZERO_E, ei = er;
+  for (int i = j + lane; i < n; i += 32) {
+    int xr, xi, yr, yi;
+    xld_exp<W, C>(p.Vm, p.Nnn, (long long)i * n + j, xr, xi);
+    xld_exp<W, C>(y, n, i, yr, yi);
+    dot_exp<true, W, C>(xr, xi, yr, yi, er, ei);
+  }
+  xfn::xfacc<W> ar, ai;
+  xfn::xfacc_init(ar, warp_max(er));
+  if constexpr (C == 2) xfn::xfacc_init(ai, warp_max(ei));
   for (int i = j + lane; i < n; i += 32) {
     cxf<W, C> x, yi;
-    cxf_load<K, W, C>(p.Vm, p.Nnn, (long long)i * n + j, x);
-    cxf_load<K, W, C>(y, n, i, yi);
-    cxf_fma<true>(dot, x, yi);
+    xld<W, C>(p.Vm, p.Nnn, (long long)i * n + j, x);
+    xld<W, C>(y, n, i, yi);
+    dot_fma<true>(ar, ai, x, yi);
   }
-  cxf_warp_sum(dot);
+  dot_finish(ar, ai, dot);
 }
 
 // |y|^2 over rows i0..n-1, every lane gets it.
 template <int K, int C>
-__device__ __forceinline__ void qr_norm2(const double* y, int n, int i0, xfn::xf<xfn::xf_words_t<K>::value>& nrm) {
+__device__ __forceinline__ void qr_norm2(const uint64_t* y, int n, int i0, xfn::xf<xfn::xf_words_t<K>::value>& nrm) {
   constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
-  cxf<W, 1> acc;
-  cxf_zero(acc);
+  int er = 2 * xfn::XF_ZERO_E, ei = er;
   for (int i = i0 + lane; i < n; i += 32) {
-    cxf<W, C> v, q;
-    cxf_load<K, W, C>(y, n, i, v);
-    cxf_mul<true>(v, v, q);
-    xfn::xf_add(acc.re, q.re, acc.re);
+    int yr, yi;
+    xld_exp<W, C>(y, n, i, yr, yi);
+    dot_exp<true, W, C>(yr, yi, yr, yi, er, ei);
   }
-  cxf_warp_sum(acc);
-  nrm = acc.re;
+  xfn::xfacc<W> ar, ai;
+  xfn::xfacc_init(ar, warp_max(er));
+  for (int i = i0 + lane; i < n; i += 32) {
+    cxf<W, C> v;
+    xld<W, C>(y, n, i, v);
+    xfn::xfacc_fma(ar, v.re, v.re);
+    if constexpr (C == 2) xfn::xfacc_fma(ar, v.im, v.im);
+  }
+  xfacc_warp_sum(ar);
+  xfn::xfacc_get(ar, nrm);
 }
 
 // w = dot + conj(s_j|x_j|) y[j] (needs the alpha flag of reflector j)
 template <int K, int C>
-__device__ __forceinline__ void qr_form_w(const QrParams& p, int j, const double* y,
+__device__ __forceinline__ void qr_form_w(const QrParams& p, int j, const uint64_t* y,
                                           const cxf<xfn::xf_words_t<K>::value, C>& dot,
                                           cxf<xfn::xf_words_t<K>::value, C>& w) {
   constexpr int W = xfn::xf_words_t<K>::value;
   cxf<W, C> sa, yj;
   cxf_load<K, W, C>(p.salpha, p.n, j, sa);
-  cxf_load<K, W, C>(y, p.n, j, yj);
+  xld<W, C>(y, p.n, j, yj);
   w = dot;
   cxf_fma<true>(w, sa, yj);
 }
 
 // y -= tau_j w v_j over rows j..n-1 (needs the ref flag of reflector j).
 template <int K, int C>
-__device__ __forceinline__ void qr_update(const QrParams& p, int j, double* y,
+__device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
                                           const cxf<xfn::xf_words_t<K>::value, C>& w) {
   constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
@@ -680,10 +764,10 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, double* y,
   for (int i = j + lane; i < n; i += 32) {
     cxf<W, C> v, yi;
     if (i == j) cxf_load<K, W, C>(p.v0, p.n, j, v);
-    else cxf_load<K, W, C>(p.Vm, p.Nnn, (long long)i * n + j, v);
-    cxf_load<K, W, C>(y, n, i, yi);
+    else xld<W, C>(p.Vm, p.Nnn, (long long)i * n + j, v);
+    xld<W, C>(y, n, i, yi);
     cxf_fma<false>(yi, ng, v);
-    cxf_store<K, W, C>(y, n, i, yi);
+    xst<W, C>(y, n, i, yi);
   }
   __syncwarp();
 }
@@ -693,7 +777,7 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, double* y,
 // x_j is out (col[j]), w = dot + conj(s_j|x_j|) y[j] as soon as s_j|x_j| and
 // v_jj are out (alpha[j]), and y -= tau_j w v_j once tau_j is out (ref[j]).
 template <int K, int C>
-__device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
+__device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
   using namespace xfn;
   constexpr int W = xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
@@ -703,9 +787,9 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
   unsigned* frinv = p.flags + 2 * n;
   unsigned* fal = p.flags + 3 * n;
   for (int i = lane; i < n; i += 32) {
-    cmd<K, C> v;
-    ld(p.A0, p.NA, (long long)i * n + c, v);
-    st(y, n, i, v);
+    cxf<W, C> v;
+    cxf_load<K, W, C>(p.A0, p.NA, (long long)i * n + c, v);
+    xst<W, C>(y, n, i, v);
   }
   __syncwarp();
   // |a_c|^2, then minus |R_jc|^2 as each R_jc is final
@@ -720,20 +804,14 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
     qr_form_w<K, C>(p, j, y, dot, w);
     if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
     qr_update<K, C>(p, j, y, w);
-    cmd<K, C> v;
-    ld(y, n, j, v);
-    if (lane == 0) st(p.Rm, p.Nnn, (long long)j * n + c, v);  // R[j][c] is final
+    if (lane == 0) xcopy<W, C>(y, n, j, p.Rm, p.Nnn, (long long)j * n + c);  // R[j][c] is final
     cxf<W, C> xv, q;
-    cxf_load<K, W, C>(y, n, j, xv);
+    xld<W, C>(y, n, j, xv);
     cxf_mul<true>(xv, xv, q);
     xf_sub(xN, q.re, xN);
   }
   // publish x_c (rows c..n-1)
-  for (int i = c + lane; i < n; i += 32) {
-    cmd<K, C> v;
-    ld(y, n, i, v);
-    st(p.Vm, p.Nnn, (long long)i * n + c, v);
-  }
+  for (int i = c + lane; i < n; i += 32) xcopy<W, C>(y, n, i, p.Vm, p.Nnn, (long long)i * n + c);
   warp_publish(&fcol[c], ep);
   // N = |x_c|^2 by downdating, recomputed when it is not positive or more
   // than 8 bits cancelled
@@ -748,7 +826,7 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
   xf_rsqrt(xN, xry);
   xf_mul(xN, xry, xal);
   cxf<W, C> x0;
-  cxf_load<K, W, C>(y, n, c, x0);
+  xld<W, C>(y, n, c, x0);
   xf<W> sre, sim;  // s|x_c|
   xf<W> sgr, sgi;  // s
   bool neg = false;
@@ -807,10 +885,11 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
   }
   if (lane == 0) {
     st_real(p.tau, p.n, c, tau);
-    cmd<K, C> r;
-    md_neg(salpha.re, r.re);
-    md_neg(salpha.im, r.im);
-    st(p.Rm, p.Nnn, (long long)c * n + c, r);
+    cxf<W, C> r;
+    r.re = sre;
+    r.im = sim;
+    cxf_neg(r);
+    xst<W, C>(p.Rm, p.Nnn, (long long)c * n + c, r);
   }
   warp_publish(&fref[c], ep);
   // 1 / R_cc = -conj(s) / |x_c|
@@ -835,16 +914,16 @@ __device__ void qr_column(const QrParams& p, int c, double* y, unsigned ep) {
 
 // Identity warp e: Q^H e_e as the reflectors appear (column e of Y = Q^H).
 template <int K, int C>
-__device__ void qr_identity(const QrParams& p, int e, double* y, unsigned ep) {
+__device__ void qr_identity(const QrParams& p, int e, uint64_t* y, unsigned ep) {
   constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   unsigned* fref = p.flags + n;
   for (int i = lane; i < n; i += 32) {
-    cmd<K, C> v;
-    cmd_zero(v);
-    if (i == e) v.re[0] = 1.0;
-    st(y, n, i, v);
+    cxf<W, C> v;
+    cxf_zero(v);
+    if (i == e) xfn::xf_from_double(1.0, v.re);
+    xst<W, C>(y, n, i, v);
   }
   __syncwarp();
   for (int j = 0; j < n; ++j) {
@@ -855,9 +934,9 @@ __device__ void qr_identity(const QrParams& p, int e, double* y, unsigned ep) {
     qr_update<K, C>(p, j, y, w);
   }
   for (int i = lane; i < n; i += 32) {
-    cmd<K, C> v;
-    ld(y, n, i, v);
-    st(p.Y, p.Nnn, (long long)i * n + e, v);
+    cxf<W, C> v;
+    xld<W, C>(y, n, i, v);
+    cxf_store<K, W, C>(p.Y, p.Nnn, (long long)i * n + e, v);
   }
 }
 
@@ -866,43 +945,47 @@ __device__ void qr_identity(const QrParams& p, int e, double* y, unsigned ep) {
 //   Z[i][i] = 1/R_ii,  Z[i][c] = -(1/R_cc) sum_{k=i..c-1} Z[i][k] R[k][c]  (c > i),
 // the block inverse of the leading (c+1) x (c+1) part of R.
 template <int K, int C>
-__device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, double* za, double* zb, unsigned ep) {
+__device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, uint64_t* za, uint64_t* zb, unsigned ep) {
   constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   unsigned* frinv = p.flags + 2 * n;
   for (int c = ia; c < n; ++c) {
     if (!warp_wait(&frinv[c], ep, p.spin_limit, p.status)) return;
-    cmd<K, C> rc;
-    ld(p.rinv, p.n, c, rc);
+    cxf<W, C> rc;
+    cxf_load<K, W, C>(p.rinv, p.n, c, rc);
     for (int q = 0; q < 2; ++q) {
       const int i = q ? ib : ia;
-      double* z = q ? zb : za;
+      uint64_t* z = q ? zb : za;
       if (c < i || (q == 1 && ib == ia)) continue;
-      cmd<K, C> zc;
+      cxf<W, C> zc;
       if (c == i) {
         zc = rc;
       } else {
-        cxf<W, C> acc;
-        cxf_zero(acc);
+        int er = 2 * xfn::XF_ZERO_E, ei = er;
+        for (int k = i + lane; k < c; k += 32) {
+          int zr, zi, rr, ri;
+          xld_exp<W, C>(z, n, k, zr, zi);
+          xld_exp<W, C>(p.Rm, p.Nnn, (long long)k * n + c, rr, ri);
+          dot_exp<false, W, C>(zr, zi, rr, ri, er, ei);
+        }
+        xfn::xfacc<W> ar, ai;
+        xfn::xfacc_init(ar, warp_max(er));
+        if constexpr (C == 2) xfn::xfacc_init(ai, warp_max(ei));
         for (int k = i + lane; k < c; k += 32) {
           cxf<W, C> zk, rk;
-          cxf_load<K, W, C>(z, n, k, zk);
-          cxf_load<K, W, C>(p.Rm, p.Nnn, (long long)k * n + c, rk);
-          cxf_fma<false>(acc, zk, rk);
+          xld<W, C>(z, n, k, zk);
+          xld<W, C>(p.Rm, p.Nnn, (long long)k * n + c, rk);
+          dot_fma<false>(ar, ai, zk, rk);
         }
-        cxf_warp_sum(acc);
-        cxf<W, C> xr, t;
-        cxf_load<K, W, C>(p.rinv, p.n, c, xr);
-        cxf_mul<false>(acc, xr, t);
-        cxf_neg(t);
-        xfn::xf_to_md<K, W>(t.re, zc.re);
-        if constexpr (C == 2) xfn::xf_to_md<K, W>(t.im, zc.im);
-        else md_zero(zc.im);
+        cxf<W, C> sum;
+        dot_finish(ar, ai, sum);
+        cxf_mul<false>(sum, rc, zc);
+        cxf_neg(zc);
       }
       if (lane == 0) {
-        st(z, n, c, zc);
-        st(p.Z, p.Nnn, (long long)i * n + c, zc);
+        xst<W, C>(z, n, c, zc);
+        cxf_store<K, W, C>(p.Z, p.Nnn, (long long)i * n + c, zc);
       }
       __syncwarp();
     }
@@ -912,11 +995,11 @@ __device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, double* za, doub
 template <int K, int C>
 __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrParams p) {
   extern __shared__ __align__(16) unsigned char qr_smem[];
-  double* sm = reinterpret_cast<double*>(qr_smem);
+  uint64_t* sm = reinterpret_cast<uint64_t*>(qr_smem);
   const int warp = threadIdx.x >> 5;
   const unsigned ep = *p.epoch;
   const int n = p.n;
-  const size_t col = (size_t)n * 2 * K;
+  const size_t col = (size_t)n * 2 * qr_xf_words(K);
   const int b = blockIdx.x;
   if (b < p.nAc) {
     const int c = b * (QR_THREADS / 32) + warp;

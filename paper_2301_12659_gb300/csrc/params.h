@@ -4,6 +4,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "xf.cuh"
 
 namespace mdn {
 
@@ -90,8 +91,8 @@ struct QrParams {
   const double* A0;
   long long NA;   // stride of the A array the A0 slice lives in
   long long Nnn;  // n*n
-  double* Rm;
-  double* Vm;
+  uint64_t* Rm;  // R and the reflectors x_j, as extended floats [W+1][C][n][n]
+  uint64_t* Vm;  // (W mantissa words and a word of exponent and sign)
   double* Y;  // Q^H (identity columns under all reflectors)
   double* Z;  // R^{-1}
   double* W;
@@ -229,9 +230,14 @@ __host__ __device__ inline long long batch_work_doubles(int K, int C, int n, int
 }
 
 
+// 64-bit words of one real extended float as the QR stores it: the
+// mantissa words and one word of exponent and sign.
+__host__ __device__ inline int qr_xf_words(int K) { return xfn::xf_words_of(K) + 1; }
 // Shared memory of a QR block: four columns of A0 or of the identity, or
-// eight rows of R^{-1} (n md values each).
-__host__ __device__ inline size_t qr_smem_bytes(int n, int K) { return 8 * (size_t)n * 2 * K * sizeof(double); }
+// eight rows of R^{-1} (n complex extended floats each).
+__host__ __device__ inline size_t qr_smem_bytes(int n, int K) {
+  return 8 * (size_t)n * 2 * qr_xf_words(K) * sizeof(uint64_t);
+}
 // Blocks of the QR launch: columns of A0 (4 per block), columns of the
 // identity (4 per block), pairs of rows of R^{-1} (4 pairs per block).
 __host__ __device__ inline int qr_blocks_for(int n) { return (n + 3) / 4 + (n + 3) / 4 + ((n + 1) / 2 + 3) / 4; }

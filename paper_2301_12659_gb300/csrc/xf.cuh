@@ -49,9 +49,11 @@ namespace xfn {
 
 constexpr int XF_ZERO_E = -(1 << 28);
 
+// 64-bit mantissa words of the xf that carries a K-limb md value
+XF_FN constexpr int xf_words_of(int K) { return K == 1 ? 1 : K == 2 ? 2 : K == 4 ? 4 : 7; }
 template <int K>
 struct xf_words_t {
-  static constexpr int value = K == 1 ? 1 : K == 2 ? 2 : K == 4 ? 4 : 7;
+  static constexpr int value = xf_words_of(K);
 };
 
 template <int W>
@@ -344,17 +346,18 @@ XF_FN void shr_words(const uint64_t (&a)[N], int s, uint64_t (&r)[N]) {
 // ---------------------------------------------------------------------------
 // fixed-point accumulation of products (dot products, convolutions)
 // ---------------------------------------------------------------------------
-// A sum of up to XF_ACC_TERMS products a_i b_i in a two's complement integer
-// T of W+2 words, worth T / 2^(64W+63) * 2^E.  E is fixed before the first
-// product from the largest exponent sum e_max = max(a_i.e + b_i.e):
-// E = e_max + 1 + XF_ACC_HEAD, so every product (< 2^(e_max+2)) enters with
-// a right shift of at least XF_ACC_HEAD bits and the sum cannot overflow.
+// A sum of fewer than XF_ACC_TERMS products a_i b_i in a two's complement
+// integer T of W+2 words, worth T / 2^(64W+63) * 2^E.  E is fixed before the
+// first product from the largest exponent sum e_max = max(a_i.e + b_i.e):
+// E = e_max + 1 + XF_ACC_HEAD, so every product (< 2^(e_max+2)) enters
+// below 2^(64W+64-XF_ACC_HEAD) with a right shift of at least XF_ACC_HEAD
+// bits, and the magnitude of the sum stays below 2^(64W+64) (W+1 words).
 // The sum is exact but for the bits shifted out below the W+1 words, so its
 // error is below (terms) 2^(XF_ACC_HEAD+1-64(W+1)) times the largest term:
 // the accuracy of an md dot product (error relative to the sum of
 // magnitudes), with 64 - XF_ACC_HEAD bits to spare.
 constexpr int XF_ACC_HEAD = 9;
-constexpr int XF_ACC_TERMS = 1 << (XF_ACC_HEAD - 1);
+constexpr int XF_ACC_TERMS = 1 << XF_ACC_HEAD;
 
 template <int W>
 struct xfacc {

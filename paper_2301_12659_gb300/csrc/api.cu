@@ -407,10 +407,10 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_Z = take(8 * KC * n * n);
   L.o_W = take(8 * KC * n * n * 2);    // A_0^{-1} of this step and of the next
   L.o_xn0 = take(8 * KC * n);          // constant coefficients of the next series
-  L.o_tau = take(8 * (size_t)ctx->K * n);
-  L.o_rinv = take(8 * KC * n);
-  L.o_salpha = take(8 * KC * n);
-  L.o_v0 = take(8 * KC * n);
+  L.o_tau = take(8 * (size_t)qr_xf_words(ctx->K) * n);  // extended floats
+  L.o_rinv = take(8 * (size_t)qr_xf_words(ctx->K) * ctx->C * n);
+  L.o_salpha = take(8 * (size_t)qr_xf_words(ctx->K) * ctx->C * n);
+  L.o_v0 = take(8 * (size_t)qr_xf_words(ctx->K) * ctx->C * n);
   L.o_fabs = take(8 * n * D);
   L.o_dxabs = take(8 * n * D);
   L.o_resabs = take(8 * n * D);
@@ -662,10 +662,10 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* 
   q.Y = ctx->at<double>(L.o_Y);
   q.Z = ctx->at<double>(L.o_Z);
   q.W = W;
-  q.tau = ctx->at<double>(L.o_tau);
-  q.rinv = ctx->at<double>(L.o_rinv);
-  q.salpha = ctx->at<double>(L.o_salpha);
-  q.v0 = ctx->at<double>(L.o_v0);
+  q.tau = ctx->at<uint64_t>(L.o_tau);
+  q.rinv = ctx->at<uint64_t>(L.o_rinv);
+  q.salpha = ctx->at<uint64_t>(L.o_salpha);
+  q.v0 = ctx->at<uint64_t>(L.o_v0);
   q.flags = ctx->at<unsigned>(L.o_flags);
   q.epoch = ctx->at<unsigned>(L.o_epoch);
   q.status = ctx->at<int>(L.o_status);

@@ -738,7 +738,7 @@ __device__ __forceinline__ void qr_form_w(const QrParams& p, int j, const uint64
                                           cxf<xfn::xf_words_t<K>::value, C>& w) {
   constexpr int W = xfn::xf_words_t<K>::value;
   cxf<W, C> sa, yj;
-  cxf_load<K, W, C>(p.salpha, p.n, j, sa);
+  xld<W, C>(p.salpha, p.n, j, sa);
   xld<W, C>(y, p.n, j, yj);
   w = dot;
   cxf_fma<true>(w, sa, yj);
@@ -751,19 +751,15 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
   constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
-  xfn::xf<W> tau;
-  {
-    double t[K];
-    ld_real(p.tau, p.n, j, t);
-    xfn::xf_from_md<K, W>(t, tau);
-  }
+  cxf<W, 1> tau;
+  xld<W, 1>(p.tau, p.n, j, tau);
   cxf<W, C> ng;
-  cxf_scale(w, tau, ng);
+  cxf_scale(w, tau.re, ng);
   cxf_neg(ng);
   __syncwarp();
   for (int i = j + lane; i < n; i += 32) {
     cxf<W, C> v, yi;
-    if (i == j) cxf_load<K, W, C>(p.v0, p.n, j, v);
+    if (i == j) xld<W, C>(p.v0, p.n, j, v);
     else xld<W, C>(p.Vm, p.Nnn, (long long)i * n + j, v);
     xld<W, C>(y, n, i, yi);
     cxf_fma<false>(yi, ng, v);
@@ -856,59 +852,52 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
     xf_mul(sgr, xal, sre);
     xf_mul(sgi, xal, sim);
   }
-  cmd<K, C> salpha, v0;
   {
-    xf<W> vr, vi;
-    xf_add(x0.re, sre, vr);
-    xf_add(x0.im, sim, vi);
-    xf_to_md<K, W>(sre, salpha.re);
-    xf_to_md<K, W>(sim, salpha.im);
-    xf_to_md<K, W>(vr, v0.re);
-    xf_to_md<K, W>(vi, v0.im);
-  }
-  if (lane == 0) {
-    st(p.salpha, p.n, c, salpha);
-    st(p.v0, p.n, c, v0);
+    cxf<W, C> sa, v0;
+    sa.re = sre;
+    sa.im = sim;
+    xf_add(x0.re, sre, v0.re);
+    xf_add(x0.im, sim, v0.im);
+    if (lane == 0) {
+      xst<W, C>(p.salpha, p.n, c, sa);
+      xst<W, C>(p.v0, p.n, c, v0);
+    }
   }
   warp_publish(&fal[c], ep);  // the later columns form their w meanwhile
-  double tau[K];
   {
-    xf<W> t1, t2, t3;
+    cxf<W, 1> tau;
+    xf_zero(tau.im);
+    xf<W> t1, t2;
     xf_mul(xal, xax0, t1);
     xf_add(xN, t1, t2);
-    xf_recip(t2, t3);
-    xf_to_md<K, W>(t3, tau);
-  }
-  if (singular) {
-    md_zero(tau);
-    if (lane == 0) atomicOr(p.status, MDN_DEV_SINGULAR);
-  }
-  if (lane == 0) {
-    st_real(p.tau, p.n, c, tau);
-    cxf<W, C> r;
-    r.re = sre;
-    r.im = sim;
-    cxf_neg(r);
-    xst<W, C>(p.Rm, p.Nnn, (long long)c * n + c, r);
+    xf_recip(t2, tau.re);
+    if (singular) {
+      xf_zero(tau.re);
+      if (lane == 0) atomicOr(p.status, MDN_DEV_SINGULAR);
+    }
+    if (lane == 0) {
+      xst<W, 1>(p.tau, p.n, c, tau);
+      cxf<W, C> r;
+      r.re = sre;
+      r.im = sim;
+      cxf_neg(r);
+      xst<W, C>(p.Rm, p.Nnn, (long long)c * n + c, r);
+    }
   }
   warp_publish(&fref[c], ep);
   // 1 / R_cc = -conj(s) / |x_c|
-  cmd<K, C> rinv;
+  cxf<W, C> rinv;
   if constexpr (C == 1) {
-    xf<W> rr = xry;  // s = +-1
-    if (!neg) xf_neg(rr);
-    xf_to_md<K, W>(rr, rinv.re);
-    md_zero(rinv.im);
+    rinv.re = xry;  // s = +-1
+    if (!neg) xf_neg(rinv.re);
+    xf_zero(rinv.im);
   } else {
-    xf<W> rr, ri;
-    xf_mul(sgr, xry, rr);
-    xf_neg(rr);
-    xf_mul(sgi, xry, ri);
-    xf_to_md<K, W>(rr, rinv.re);
-    xf_to_md<K, W>(ri, rinv.im);
+    xf_mul(sgr, xry, rinv.re);
+    xf_neg(rinv.re);
+    xf_mul(sgi, xry, rinv.im);
   }
-  if (singular) cmd_zero(rinv);
-  if (lane == 0) st(p.rinv, p.n, c, rinv);
+  if (singular) cxf_zero(rinv);
+  if (lane == 0) xst<W, C>(p.rinv, p.n, c, rinv);
   warp_publish(&frinv[c], ep);
 }
 
@@ -953,7 +942,7 @@ __device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, uint64_t* za, ui
   for (int c = ia; c < n; ++c) {
     if (!warp_wait(&frinv[c], ep, p.spin_limit, p.status)) return;
     cxf<W, C> rc;
-    cxf_load<K, W, C>(p.rinv, p.n, c, rc);
+    xld<W, C>(p.rinv, p.n, c, rc);
     for (int q = 0; q < 2; ++q) {
       const int i = q ? ib : ia;
       uint64_t* z = q ? zb : za;
@@ -1082,19 +1071,54 @@ __device__ __forceinline__ void st_acc(double* p, long long N, long long i, cons
 // sum_l M[row_off + l*ms] x_l over the warp (a row of a row-major n-by-n
 // block for ms = 1, a column for ms = n) with x_l = coefficient kx of
 // variable l; all lanes get it.
+// For K >= 2 the products are summed in one fixed-point accumulator per
+// part (xf.cuh) at a scale set by a warp maximum of the exponent sums, taken
+// from the leading limbs (an md value is below 2^(e0+1) for a leading limb
+// in [2^e0, 2^(e0+1)); one more bit covers a last-limb carry), so the warp
+// sum is an integer sum and the result is rounded to K limbs once.
+__device__ __forceinline__ int lead_exp(double x) {
+  const int E = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
+  return E == 0 ? 2 * xfn::XF_ZERO_E : E - 1023;
+}
 template <int K, int C>
 __device__ __forceinline__ void warp_rowdot(const double* Mp, long long NM, long long row_off, int ms,
                                             const double* xp, long long Nx, int n, int D, int kx, cmd<K, C>& out) {
   const int lane = threadIdx.x & 31;
-  CAcc<K, C> acc;
-  cacc_zero(acc);
-  for (int l = lane; l < n; l += 32) {
-    cmd<K, C> a, x;
-    ld(Mp, NM, row_off + (long long)l * ms, a);
-    ld(xp, Nx, (long long)l * D + kx, x);
-    cacc_fma(acc, a, x);
+  if constexpr (K >= 2) {
+    constexpr int W = xfn::xf_words_t<K>::value;
+    int er = 4 * xfn::XF_ZERO_E, ei = er;
+    for (int l = lane; l < n; l += 32) {
+      const long long ia = row_off + (long long)l * ms, ix = (long long)l * D + kx;
+      const int ar = lead_exp(Mp[ia]), xr = lead_exp(xp[ix]);
+      const int ai = C == 2 ? lead_exp(Mp[NM + ia]) : 2 * xfn::XF_ZERO_E;
+      const int xi = C == 2 ? lead_exp(xp[Nx + ix]) : 2 * xfn::XF_ZERO_E;
+      dot_exp<false, W, C>(ar, ai, xr, xi, er, ei);
+    }
+    xfn::xfacc<W> acr, aci;
+    xfn::xfacc_init(acr, warp_max(er) + 1);
+    if constexpr (C == 2) xfn::xfacc_init(aci, warp_max(ei) + 1);
+    for (int l = lane; l < n; l += 32) {
+      cxf<W, C> a, x;
+      cxf_load<K, W, C>(Mp, NM, row_off + (long long)l * ms, a);
+      cxf_load<K, W, C>(xp, Nx, (long long)l * D + kx, x);
+      dot_fma<false>(acr, aci, a, x);
+    }
+    cxf<W, C> sum;
+    dot_finish(acr, aci, sum);
+    xfn::xf_to_md<K, W>(sum.re, out.re);
+    if constexpr (C == 2) xfn::xf_to_md<K, W>(sum.im, out.im);
+    else md_zero(out.im);
+  } else {
+    CAcc<K, C> acc;
+    cacc_zero(acc);
+    for (int l = lane; l < n; l += 32) {
+      cmd<K, C> a, x;
+      ld(Mp, NM, row_off + (long long)l * ms, a);
+      ld(xp, Nx, (long long)l * D + kx, x);
+      cacc_fma(acc, a, x);
+    }
+    warp_sum_acc(acc, out);
   }
-  warp_sum_acc(acc, out);
 }
 
 template <int K, int C>

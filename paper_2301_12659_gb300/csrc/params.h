@@ -96,10 +96,11 @@ struct QrParams {
   double* Y;  // Q^H (identity columns under all reflectors)
   double* Z;  // R^{-1}
   double* W;
-  double* tau;     // [K][n]
-  double* rinv;    // [K][C][n]
-  double* salpha;  // [K][C][n] s_j |x_j| (R_jj = -salpha_j)
-  double* v0;      // [K][C][n] leading entry of reflector j
+  // scalars of reflector j, as extended floats ([W+1][n] or [W+1][C][n])
+  uint64_t* tau;
+  uint64_t* rinv;    // 1 / R_jj
+  uint64_t* salpha;  // s_j |x_j| (R_jj = -salpha_j)
+  uint64_t* v0;      // leading entry of reflector j
   unsigned* flags;  // [4n]: column, reflector (tau), 1/R_jj, and s_j|x_j| with v_jj published
   const unsigned* epoch;
   int* status;

@@ -25,7 +25,9 @@
 //     and 1/sqrt(a) (y += y(1 - ay), y += y(1 - ay^2)/2), started from the
 //     double precision reciprocal / reciprocal square root of the leading
 //     53 bits, each step at the narrowest width that holds the bits it
-//     makes correct, until all 64W bits are;
+//     makes correct: the reciprocal to the md precision (within 2K^2
+//     units of 2^(-53K), the bound of the md operations), the reciprocal
+//     square root to 64W bits;
 //   * xf -> md: K times, the leading 53 bits rounded to nearest give a limb
 //     and the exact remainder goes on, so the limbs are nonoverlapping with
 //     |limb_{l+1}| <= ulp(limb_l)/2.
@@ -584,9 +586,13 @@ XF_FN void newton_at(const xf<W>& a, xf<W>& y) {
   xf_resize<W>(yv, y);
 }
 // From a 53-bit seed each step doubles the correct bits up to the width it
-// runs at, so the early steps run narrower: widths 1; 1, 2; 2, 4, 4;
-// 2, 4, 7, 7 for W = 1, 2, 4, 7 (53 -> 64; 64 -> 128; 106 -> 212 -> 256;
-// 106 -> 212 -> 424 -> 448 bits).
+// runs at, so the early steps run narrower.  The reciprocal, seeded with the
+// correctly rounded double reciprocal of the leading 53 bits, stops for
+// W <= 4 once about the 53K bits of the md value it serves are correct:
+// widths 1; 1, 2; 2, 4 for W = 1, 2, 4 (53 -> 64; -> 128; -> 106 -> 212
+// bits, less a few for the truncated seed).  The reciprocal square root
+// (a seed of about 52 bits, a step that squares 3/2 of the error) and the
+// octo double widths take one more full-width step: 64W bits.
 template <bool RSQRT, int W>
 XF_FN void newton_steps(const xf<W>& a, xf<W>& y) {
   if constexpr (W == 1) {
@@ -597,7 +603,7 @@ XF_FN void newton_steps(const xf<W>& a, xf<W>& y) {
   } else if constexpr (W <= 4) {
     newton_at<2, RSQRT>(a, y);
     newton_at<W, RSQRT>(a, y);
-    newton_at<W, RSQRT>(a, y);
+    if constexpr (RSQRT) newton_at<W, RSQRT>(a, y);
   } else {
     newton_at<2, RSQRT>(a, y);
     newton_at<4, RSQRT>(a, y);

@@ -15,7 +15,9 @@ from CUDA events around each timed step (inputs resident in HBM, L2 flushed
 between steps); ``e2e`` times whole solves through the public API with the
 start series copied from pinned host memory and the solution copied back;
 ``roofline`` reports the phase with the largest share of device time against
-the FP64 pipe peak; ``cpu_baseline`` times the CPU oracle on a bounded sample.
+the integer pipe peak (its md multiply-adds x the integer instructions one
+costs in integer limbs); ``cpu_baseline`` times the CPU oracle on a bounded
+sample.
 
 ``--impl reference`` times the CPU oracle (the plain multiple double
 implementation the tests check the GPU against) on the same workload.
@@ -45,6 +47,17 @@ FP64_LANES_PER_CLK_PER_SM = 1.684
 NUM_SMS = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_OPS = NUM_SMS * FP64_LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
+# Integer pipe peak: 152 SMs x 64 integer lane operations per clock per SM
+# (measured: IMAD and LOP3 each) x 2070 MHz.  The evaluation, the QR and the
+# forward substitution compute md values in integer limbs (extended floats
+# and fixed-point accumulators), so their roofline is this pipe.
+INT_LANES_PER_CLK_PER_SM = 64
+INT_PEAK_OPS = NUM_SMS * INT_LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
+# Integer thread instructions per md multiply-add in integer limbs, by
+# limbs (real data): measured with ncu on ed_kernel at the quad double
+# workload, 2.976e9 integer instructions for 12 104 x 528 = 6.39e6
+# multiply-adds (operand conversions and the accumulator included).
+XF_INT_OPS_PER_FMA = {4: 466.0}
 
 METRIC = "Newton steps/s (qd, n=64, d=31)"
 
@@ -88,9 +101,9 @@ def parse():
 # capture of the unchanged kernels (profiles/ncu_qr_ed_fsub_qd-real-n64-d31.md);
 # absent entries report null.
 NCU_TRAFFIC = {
-    ("qd-real-n64-d31", "qr"): 612864 + 42240,
-    ("qd-real-n64-d31", "evaluate"): 1265664,
-    ("qd-real-n64-d31", "forward"): 4604416 + 30720,
+    ("qd-real-n64-d31", "qr"): 595712 + 8704,
+    ("qd-real-n64-d31", "evaluate"): 1301504,
+    ("qd-real-n64-d31", "forward"): 4636672 + 47872,
 }
 
 
@@ -368,7 +381,9 @@ def run_adjoint(args, dev):
                         "frac": counts["fp64_ops"] / (ms * 1e-3) / FP64_PEAK_OPS,
                         "dominant_kernel": "qr",
                         "qr_frac": counts["qr_fp64_ops"] / (qr_ms * 1e-3) / FP64_PEAK_OPS if qr_ms > 0 else None,
-                        "peak": FP64_PEAK_OPS / 1e12, "unit": "FP64 Tops/s"},
+                        "peak": FP64_PEAK_OPS / 1e12, "unit": "FP64 Tops/s",
+                        "note": "FP64-equivalent: the md algorithms' FP64 operation count against the FP64 "
+                                "pipe; the QR, the evaluation and the solve run in integer limbs"},
            "gradient_entries": int(grad.numel() // acfg.K), "loss_leading": float(loss[0]),
            "phases_ms_per_gradient": {p: float(v) / reps for p, v in zip(md.PHASES, phase_ms)}}
     nw.close()
@@ -473,25 +488,39 @@ def run_ours(args, cfg):
     # roofline of the phase with the largest share of device time
     counts = F.step_counts(s.monomial_sizes(), s.n, s.D, s.K, s.C)
     steps_timed = args.steps
-    per_phase_ops = {"evaluate": counts["evaluate"]["fp64_ops"], "qr": counts["solve"]["qr_fp64_ops"],
-                     "forward": counts["solve"]["forward_fp64_ops"]}
     share = {p: float(ms) for p, ms in zip(md.PHASES, phase_ms)}
-    dom = max(per_phase_ops, key=lambda p: share[p])
+    md_fma = {"evaluate": counts["evaluate"]["md_fma"], "qr": counts["solve"]["qr_md_fma"],
+              "forward": counts["solve"]["forward_md_fma"]}
+    dom = max(md_fma, key=lambda p: share[p])
     dom_launch_ms = share[dom] / steps_timed
-    achieved = per_phase_ops[dom] / (dom_launch_ms * 1e-3)
     eval_ms = share["evaluate"] / steps_timed
+    unit_cost = XF_INT_OPS_PER_FMA.get(cfg.K) if cfg.C == 1 else None
+    if unit_cost:
+        # algorithmic md multiply-adds x integer instructions per multiply-add
+        per_phase_ops = {p: v * unit_cost for p, v in md_fma.items()}
+        peak, unit = INT_PEAK_OPS, "int Tops/s"
+        peak_source = "derived: 152 SMs x 64 integer lanes/clk/SM (measured IMAD/LOP3) x 2070 MHz"
+        work = f"{md_fma[dom]} md multiply-adds x {unit_cost:g} integer instructions each (ncu, ed_kernel)"
+    else:
+        # no measured integer cost for these limbs: FP64 operations of the md
+        # algorithms against the FP64 pipe
+        per_phase_ops = {"evaluate": counts["evaluate"]["fp64_ops"], "qr": counts["solve"]["qr_fp64_ops"],
+                         "forward": counts["solve"]["forward_fp64_ops"]}
+        peak, unit = FP64_PEAK_OPS, "FP64 Tops/s"
+        peak_source = "derived: 152 SMs x 1.684 FP64 lanes/clk/SM (measured) x 2070 MHz"
+        work = "FP64 operations of the md algorithms (flops.py)"
+    achieved = per_phase_ops[dom] / (dom_launch_ms * 1e-3)
     line = {
         "metric": metric_of(cfg), "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(cfg), "data": "synthetic",
         "config": config_dict(cfg, args),
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": FP64_PEAK_OPS / 1e12,
-                     "unit": "FP64 Tops/s", "frac": achieved / FP64_PEAK_OPS,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": unit, "frac": achieved / peak,
                      "traffic": NCU_TRAFFIC.get((cfg.name, dom)),
-                     "peak_source": "derived: 152 SMs x 1.684 FP64 lanes/clk/SM (measured) x 2070 MHz",
-                     "ops_per_launch": per_phase_ops[dom]},
+                     "peak_source": peak_source, "ops_per_launch": per_phase_ops[dom], "work": work},
         "phases_ms_per_step": {p: share[p] / steps_timed for p in md.PHASES},
-        "evaluate_roofline_frac": (per_phase_ops["evaluate"] / (eval_ms * 1e-3)) / FP64_PEAK_OPS if eval_ms > 0 else None,
+        "evaluate_roofline_frac": (per_phase_ops["evaluate"] / (eval_ms * 1e-3)) / peak if eval_ms > 0 else None,
         "step_fp64_ops": counts["fp64_ops"], "step_paper_flops": counts["paper_flops"],
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": nbytes / cfg.steps,
                 "d2h_bytes_per_step": (nbytes + 24 * cfg.steps) / cfg.steps,

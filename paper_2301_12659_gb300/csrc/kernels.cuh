@@ -757,13 +757,21 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
   cxf_scale(w, tau.re, ng);
   cxf_neg(ng);
   __syncwarp();
-  for (int i = j + lane; i < n; i += 32) {
-    cxf<W, C> v, yi;
+  // two rows per pass (i and i + 32): two independent chains to interleave
+  for (int i = j + lane; i < n; i += 64) {
+    const int i2 = i + 32;
+    const bool two = i2 < n;
+    cxf<W, C> v, yi, v2, y2;
     if (i == j) xld<W, C>(p.v0, p.n, j, v);
     else xld<W, C>(p.Vm, p.Nnn, (long long)i * n + j, v);
     xld<W, C>(y, n, i, yi);
+    const int r2 = two ? i2 : i;
+    xld<W, C>(p.Vm, p.Nnn, (long long)r2 * n + j, v2);
+    xld<W, C>(y, n, r2, y2);
     cxf_fma<false>(yi, ng, v);
+    cxf_fma<false>(y2, ng, v2);
     xst<W, C>(y, n, i, yi);
+    if (two) xst<W, C>(y, n, i2, y2);
   }
   __syncwarp();
 }

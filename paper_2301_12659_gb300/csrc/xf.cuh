@@ -575,6 +575,33 @@ XF_FN void rsqrt_step(const xf<V>& a, xf<V>& y) {
   xf_add(y, u, t);
   y = t;
 }
+// one third-order step for 1/sqrt(a) at width V: with e = 1 - a y^2,
+// y += y (e/2 + 3e^2/8), which cubes the relative error (to 5/16 of it)
+template <int V>
+XF_FN void rsqrt_step3(const xf<V>& a, xf<V>& y) {
+  xf<V> one, t, u, e, c38, h;
+  xf_from_double(1.0, one);
+  xf_from_double(0.375, c38);
+  xf_mul(a, y, t);
+  xf_mul(t, y, u);
+  xf_sub(one, u, e);
+  xf_mul(e, c38, t);
+  xf_from_double(0.5, u);
+  xf_add(u, t, h);
+  xf_mul(e, h, t);
+  xf_mul(y, t, u);
+  xf_add(y, u, t);
+  y = t;
+}
+// the third-order step at width V on the W-word a and y
+template <int V, int W>
+XF_FN void rsqrt3_at(const xf<W>& a, xf<W>& y) {
+  xf<V> av, yv;
+  xf_resize<V>(a, av);
+  xf_resize<V>(y, yv);
+  rsqrt_step3<V>(av, yv);
+  xf_resize<W>(yv, y);
+}
 // the step at width V on the W-word a and y
 template <int V, bool RSQRT, int W>
 XF_FN void newton_at(const xf<W>& a, xf<W>& y) {
@@ -590,11 +617,18 @@ XF_FN void newton_at(const xf<W>& a, xf<W>& y) {
 // correctly rounded double reciprocal of the leading 53 bits, stops for
 // W <= 4 once about the 53K bits of the md value it serves are correct:
 // widths 1; 1, 2; 2, 4 for W = 1, 2, 4 (53 -> 64; -> 128; -> 106 -> 212
-// bits, less a few for the truncated seed).  The reciprocal square root
-// (a seed of about 52 bits, a step that squares 3/2 of the error) and the
-// octo double widths take one more full-width step: 64W bits.
+// bits, less a few for the truncated seed); the octo double width takes one
+// more full-width step (64W bits).  The reciprocal square root (a seed of
+// about 52 bits) starts with a third-order step at 2 words (-> 125 bits)
+// and then doubles: widths 2; 2, 4; 2, 4, 7 for W = 2, 4, 7 (64W bits).
 template <bool RSQRT, int W>
 XF_FN void newton_steps(const xf<W>& a, xf<W>& y) {
+  if constexpr (RSQRT && W >= 2) {
+    rsqrt3_at<2>(a, y);
+    if constexpr (W >= 4) newton_at<4, true>(a, y);
+    if constexpr (W > 4) newton_at<W, true>(a, y);
+    return;
+  }
   if constexpr (W == 1) {
     newton_at<1, RSQRT>(a, y);
   } else if constexpr (W == 2) {

@@ -689,11 +689,13 @@ static double norm1(const mdc *v, long N, int C) {
     return s;
 }
 
-/* ||B - T DX||_1 with T the block Toeplitz matrix, every entry in md. */
+/* ||B - T DX||_1 with T the block Toeplitz matrix, every entry in md.  The
+   entries' magnitudes are summed in row-major order after the parallel loop,
+   so the reported norm does not depend on the thread count. */
 static double toeplitz_residual(int K, int C, int n, int d, const mdc *A, const mdc *B, const mdc *DX) {
     const int D = d + 1;
-    double total = 0.0;
-#pragma omp parallel for schedule(static) reduction(+ : total)
+    double *mag = (double *)malloc(sizeof(double) * (size_t)n * D);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
         cacc_t *t = (cacc_t *)malloc(sizeof(cacc_t));
         for (int k = 0; k < D; ++k) {
@@ -704,10 +706,13 @@ static double toeplitz_residual(int K, int C, int n, int d, const mdc *A, const 
                 for (int l = 0; l < n; ++l)
                     cacc_add_prod(t, &A[((size_t)j * n + i) * n + l], &DX[(size_t)l * D + (k - j)], K, C, -1.0);
             cacc_round(t, K, C, &r);
-            total += norm1(&r, 1, C);
+            mag[(size_t)i * D + k] = norm1(&r, 1, C);
         }
         free(t);
     }
+    double total = 0.0;
+    for (long e = 0; e < (long)n * D; ++e) total += mag[e];
+    free(mag);
     return total;
 }
 

@@ -272,9 +272,10 @@ void mdn_batch_destroy(mdn_batch* b);
 
 /* f(x(t)) without a context, a workspace or any device allocation.  The
  * paper has no counterpart: this entry point exists for callers that cannot
- * allocate device memory (code running while a CUDA graph is captured,
- * plug-ins inside an application that owns the device allocator, loops that
- * must not allocate after start-up).  The scratch of the evaluation lives in
+ * allocate device memory (plug-ins inside an application whose own pool
+ * reserves the device memory up front, so that a cudaMalloc of theirs would
+ * fail or fragment it; real-time loops that must not allocate after start-up,
+ * since cudaMalloc can block on the device).  The scratch of the evaluation lives in
  * one file-scope device array of MDN_STATIC_SCRATCH_BYTES that every GPU
  * loading the library keeps until the process exits.
  *   All pointers are device pointers in the layouts above: eq_of_monomial [M],

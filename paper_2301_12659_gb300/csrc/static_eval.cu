@@ -2,9 +2,10 @@
 // mdn_evaluate_static() for callers that cannot allocate device memory.
 //
 // Some callers of this library cannot call cudaMalloc or any allocating
-// routine: code that runs while a CUDA graph is being captured, plugins that
-// live inside a host application which owns the device allocator, or
-// real-time loops that must not allocate after start-up.  For them this file
+// routine: plug-ins inside a host application whose own pool reserves the
+// device memory up front (a cudaMalloc of theirs would fail or fragment that
+// pool), or real-time loops that must not allocate after start-up (cudaMalloc
+// can block on the device).  For them this file
 // keeps the scratch of the evaluation (the running forward products of each
 // monomial, two series per equation) in one file-scope device array,
 // g_scratch, of MDN_STATIC_SCRATCH_BYTES.  Every GPU that loads the library

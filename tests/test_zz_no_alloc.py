@@ -1,6 +1,7 @@
 """mdn_evaluate_static: the evaluation for callers that cannot allocate device
-memory (code running under CUDA graph capture, plug-ins inside an application
-that owns the allocator, loops that must not allocate after start-up).  Its
+memory (plug-ins inside an application whose own pool reserves the device
+memory up front, loops that must not allocate after start-up because
+cudaMalloc can block on the device).  Its
 scratch is a static device array of the library, so nothing is allocated per
 call.  Checked against the workspace evaluation (mdn_evaluate) on two calls
 in a row, within the per-precision tolerances of the other GPU tests.

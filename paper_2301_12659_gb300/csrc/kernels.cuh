@@ -639,15 +639,7 @@ __device__ __forceinline__ void xfacc_warp_sum(xfn::xfacc<W>& a) {
     uint64_t o[W + 2];
 #pragma unroll
     for (int i = 0; i < W + 2; ++i) o[i] = __shfl_xor_sync(FULL, a.w[i], off);
-    uint64_t c = 0;
-#pragma unroll
-    for (int i = 0; i < W + 2; ++i) {
-      const uint64_t u = a.w[i] + o[i];
-      const uint64_t c1 = u < o[i];
-      const uint64_t v = u + c;
-      c = c1 | (v < u);
-      a.w[i] = v;
-    }
+    xfn::add_words<W + 2>(a.w, o, 0ULL);
   }
 }
 

@@ -123,6 +123,200 @@ XF_FN uint64_t fshl(uint64_t lo, uint64_t hi, int b) {
   return b == 0 ? hi : ((hi << b) | (lo >> (64 - b)));
 }
 
+// Carry chains.  On the device they are single inline-PTX blocks of add.cc /
+// addc.cc, so the carry travels in the condition code from word to word
+// (one add per word) instead of being rebuilt from unsigned compares; the
+// condition code lives only inside each block.
+#if defined(__CUDACC__)
+template <int N>
+struct addc_ptx;
+template <>
+struct addc_ptx<2> {
+  static __device__ __forceinline__ uint64_t run(uint64_t (&a)[2], const uint64_t (&b)[2], uint64_t cin) {
+    uint64_t cout;
+    asm("{\n\t"
+        ".reg .u64 t;\n\t"
+        "add.cc.u64 t, %5, 0xffffffffffffffff;\n\t"
+        "addc.cc.u64 %0, %0, %3;\n\t"
+        "addc.cc.u64 %1, %1, %4;\n\t"
+        "addc.u64 %2, 0, 0;\n\t"
+        "}"
+        : "+l"(a[0]), "+l"(a[1]), "=l"(cout)
+        : "l"(b[0]), "l"(b[1]), "l"(cin));
+    return cout;
+  }
+};
+template <>
+struct addc_ptx<3> {
+  static __device__ __forceinline__ uint64_t run(uint64_t (&a)[3], const uint64_t (&b)[3], uint64_t cin) {
+    uint64_t cout;
+    asm("{\n\t"
+        ".reg .u64 t;\n\t"
+        "add.cc.u64 t, %7, 0xffffffffffffffff;\n\t"
+        "addc.cc.u64 %0, %0, %4;\n\t"
+        "addc.cc.u64 %1, %1, %5;\n\t"
+        "addc.cc.u64 %2, %2, %6;\n\t"
+        "addc.u64 %3, 0, 0;\n\t"
+        "}"
+        : "+l"(a[0]), "+l"(a[1]), "+l"(a[2]), "=l"(cout)
+        : "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(cin));
+    return cout;
+  }
+};
+template <>
+struct addc_ptx<4> {
+  static __device__ __forceinline__ uint64_t run(uint64_t (&a)[4], const uint64_t (&b)[4], uint64_t cin) {
+    uint64_t cout;
+    asm("{\n\t"
+        ".reg .u64 t;\n\t"
+        "add.cc.u64 t, %9, 0xffffffffffffffff;\n\t"
+        "addc.cc.u64 %0, %0, %5;\n\t"
+        "addc.cc.u64 %1, %1, %6;\n\t"
+        "addc.cc.u64 %2, %2, %7;\n\t"
+        "addc.cc.u64 %3, %3, %8;\n\t"
+        "addc.u64 %4, 0, 0;\n\t"
+        "}"
+        : "+l"(a[0]), "+l"(a[1]), "+l"(a[2]), "+l"(a[3]), "=l"(cout)
+        : "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(b[3]), "l"(cin));
+    return cout;
+  }
+};
+template <>
+struct addc_ptx<5> {
+  static __device__ __forceinline__ uint64_t run(uint64_t (&a)[5], const uint64_t (&b)[5], uint64_t cin) {
+    uint64_t cout;
+    asm("{\n\t"
+        ".reg .u64 t;\n\t"
+        "add.cc.u64 t, %11, 0xffffffffffffffff;\n\t"
+        "addc.cc.u64 %0, %0, %6;\n\t"
+        "addc.cc.u64 %1, %1, %7;\n\t"
+        "addc.cc.u64 %2, %2, %8;\n\t"
+        "addc.cc.u64 %3, %3, %9;\n\t"
+        "addc.cc.u64 %4, %4, %10;\n\t"
+        "addc.u64 %5, 0, 0;\n\t"
+        "}"
+        : "+l"(a[0]), "+l"(a[1]), "+l"(a[2]), "+l"(a[3]), "+l"(a[4]), "=l"(cout)
+        : "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(b[3]), "l"(b[4]), "l"(cin));
+    return cout;
+  }
+};
+template <>
+struct addc_ptx<6> {
+  static __device__ __forceinline__ uint64_t run(uint64_t (&a)[6], const uint64_t (&b)[6], uint64_t cin) {
+    uint64_t cout;
+    asm("{\n\t"
+        ".reg .u64 t;\n\t"
+        "add.cc.u64 t, %13, 0xffffffffffffffff;\n\t"
+        "addc.cc.u64 %0, %0, %7;\n\t"
+        "addc.cc.u64 %1, %1, %8;\n\t"
+        "addc.cc.u64 %2, %2, %9;\n\t"
+        "addc.cc.u64 %3, %3, %10;\n\t"
+        "addc.cc.u64 %4, %4, %11;\n\t"
+        "addc.cc.u64 %5, %5, %12;\n\t"
+        "addc.u64 %6, 0, 0;\n\t"
+        "}"
+        : "+l"(a[0]), "+l"(a[1]), "+l"(a[2]), "+l"(a[3]), "+l"(a[4]), "+l"(a[5]), "=l"(cout)
+        : "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(b[3]), "l"(b[4]), "l"(b[5]), "l"(cin));
+    return cout;
+  }
+};
+template <>
+struct addc_ptx<7> {
+  static __device__ __forceinline__ uint64_t run(uint64_t (&a)[7], const uint64_t (&b)[7], uint64_t cin) {
+    uint64_t cout;
+    asm("{\n\t"
+        ".reg .u64 t;\n\t"
+        "add.cc.u64 t, %15, 0xffffffffffffffff;\n\t"
+        "addc.cc.u64 %0, %0, %8;\n\t"
+        "addc.cc.u64 %1, %1, %9;\n\t"
+        "addc.cc.u64 %2, %2, %10;\n\t"
+        "addc.cc.u64 %3, %3, %11;\n\t"
+        "addc.cc.u64 %4, %4, %12;\n\t"
+        "addc.cc.u64 %5, %5, %13;\n\t"
+        "addc.cc.u64 %6, %6, %14;\n\t"
+        "addc.u64 %7, 0, 0;\n\t"
+        "}"
+        : "+l"(a[0]), "+l"(a[1]), "+l"(a[2]), "+l"(a[3]), "+l"(a[4]), "+l"(a[5]), "+l"(a[6]), "=l"(cout)
+        : "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(b[3]), "l"(b[4]), "l"(b[5]), "l"(b[6]), "l"(cin));
+    return cout;
+  }
+};
+template <>
+struct addc_ptx<8> {
+  static __device__ __forceinline__ uint64_t run(uint64_t (&a)[8], const uint64_t (&b)[8], uint64_t cin) {
+    uint64_t cout;
+    asm("{\n\t"
+        ".reg .u64 t;\n\t"
+        "add.cc.u64 t, %17, 0xffffffffffffffff;\n\t"
+        "addc.cc.u64 %0, %0, %9;\n\t"
+        "addc.cc.u64 %1, %1, %10;\n\t"
+        "addc.cc.u64 %2, %2, %11;\n\t"
+        "addc.cc.u64 %3, %3, %12;\n\t"
+        "addc.cc.u64 %4, %4, %13;\n\t"
+        "addc.cc.u64 %5, %5, %14;\n\t"
+        "addc.cc.u64 %6, %6, %15;\n\t"
+        "addc.cc.u64 %7, %7, %16;\n\t"
+        "addc.u64 %8, 0, 0;\n\t"
+        "}"
+        : "+l"(a[0]), "+l"(a[1]), "+l"(a[2]), "+l"(a[3]), "+l"(a[4]), "+l"(a[5]), "+l"(a[6]), "+l"(a[7]), "=l"(cout)
+        : "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(b[3]), "l"(b[4]), "l"(b[5]), "l"(b[6]), "l"(b[7]), "l"(cin));
+    return cout;
+  }
+};
+template <>
+struct addc_ptx<9> {
+  static __device__ __forceinline__ uint64_t run(uint64_t (&a)[9], const uint64_t (&b)[9], uint64_t cin) {
+    uint64_t cout;
+    asm("{\n\t"
+        ".reg .u64 t;\n\t"
+        "add.cc.u64 t, %19, 0xffffffffffffffff;\n\t"
+        "addc.cc.u64 %0, %0, %10;\n\t"
+        "addc.cc.u64 %1, %1, %11;\n\t"
+        "addc.cc.u64 %2, %2, %12;\n\t"
+        "addc.cc.u64 %3, %3, %13;\n\t"
+        "addc.cc.u64 %4, %4, %14;\n\t"
+        "addc.cc.u64 %5, %5, %15;\n\t"
+        "addc.cc.u64 %6, %6, %16;\n\t"
+        "addc.cc.u64 %7, %7, %17;\n\t"
+        "addc.cc.u64 %8, %8, %18;\n\t"
+        "addc.u64 %9, 0, 0;\n\t"
+        "}"
+        : "+l"(a[0]), "+l"(a[1]), "+l"(a[2]), "+l"(a[3]), "+l"(a[4]), "+l"(a[5]), "+l"(a[6]), "+l"(a[7]), "+l"(a[8]), "=l"(cout)
+        : "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(b[3]), "l"(b[4]), "l"(b[5]), "l"(b[6]), "l"(b[7]), "l"(b[8]), "l"(cin));
+    return cout;
+  }
+};
+
+#endif
+
+// a = a + b + cin (mod 2^(64N)), cin in {0, 1}; returns the carry out
+template <int N>
+XF_FN uint64_t add_words(uint64_t (&a)[N], const uint64_t (&b)[N], uint64_t cin) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (N >= 2 && N <= 9) return addc_ptx<N>::run(a, b, cin);
+#endif
+  uint64_t c = cin;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const uint64_t u = a[i] + b[i];
+    const uint64_t c1 = u < b[i];
+    const uint64_t v = u + c;
+    c = c1 | (v < u);
+    a[i] = v;
+  }
+  return c;
+}
+
+// (c:s) += v: a word added into a sum s whose carries are counted in c
+XF_FN void add_count(uint64_t& s, uint64_t& c, uint64_t v) {
+#if defined(__CUDA_ARCH__)
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(s), "+l"(c) : "l"(v));
+#else
+  s += v;
+  c += s < v;
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // mantissa shifts and normalisation
 // ---------------------------------------------------------------------------
@@ -235,33 +429,28 @@ XF_FN void xf_add(const xf<W>& a, const xf<W>& b, xf<W>& r) {
   shr_guard<W>(y.m, d, ys);
   uint64_t g[W + 2];
   if (x.s == y.s) {
-    uint64_t c = 0;
+    uint64_t t[W], u[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      t[i] = x.m[i];
+      u[i] = ys[i + 1];
+    }
     g[0] = ys[0];
+    g[W + 1] = add_words<W>(t, u, 0ULL);
 #pragma unroll
-    for (int i = 0; i < W; ++i) {
-      const uint64_t u = x.m[i] + ys[i + 1];
-      const uint64_t c1 = u < x.m[i];
-      const uint64_t v = u + c;
-      c = c1 | (v < u);
-      g[i + 1] = v;
-    }
-    g[W + 1] = c;
+    for (int i = 0; i < W; ++i) g[i + 1] = t[i];
   } else {
-    uint64_t bw = 0;
-    // guard word of x is zero
-    {
-      const uint64_t v = 0ULL - ys[0];
-      bw = ys[0] != 0ULL;
-      g[0] = v;
-    }
+    // (x.m with a zero guard word) - ys = (x.m : 0) + ~ys + 1; no borrow
+    // since |x| >= |y|
+    uint64_t t[W + 1], u[W + 1];
+    t[0] = 0ULL;
 #pragma unroll
-    for (int i = 0; i < W; ++i) {
-      const uint64_t u = x.m[i] - ys[i + 1];
-      const uint64_t b1 = x.m[i] < ys[i + 1];
-      const uint64_t v = u - bw;
-      bw = b1 | (u < bw);
-      g[i + 1] = v;
-    }
+    for (int i = 0; i < W; ++i) t[i + 1] = x.m[i];
+#pragma unroll
+    for (int i = 0; i <= W; ++i) u[i] = ~ys[i];
+    add_words<W + 1>(t, u, 1ULL);
+#pragma unroll
+    for (int i = 0; i <= W; ++i) g[i] = t[i];
     g[W + 1] = 0ULL;
   }
   // g (W+2 words) has its leading bit at 64(W+1) or below; the value is
@@ -293,17 +482,9 @@ XF_FN void xf_mul_core(const xf<W>& a, const xf<W>& b, uint64_t (&h)[W + 1]) {
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       const int j = k - i;
-      if (j >= 0 && j < W) {
-        const uint64_t lo = a.m[i] * b.m[j];
-        s += lo;
-        c += s < lo;
-      }
+      if (j >= 0 && j < W) add_count(s, c, a.m[i] * b.m[j]);
       const int jh = k - 1 - i;
-      if (jh >= 0 && jh < W && k - 1 >= W - 2) {
-        const uint64_t hi = umulhi(a.m[i], b.m[jh]);
-        s += hi;
-        c += s < hi;
-      }
+      if (jh >= 0 && jh < W && k - 1 >= W - 2) add_count(s, c, umulhi(a.m[i], b.m[jh]));
     }
     if (k >= W - 1) h[k - (W - 1)] = s;
     carry = c;
@@ -390,17 +571,13 @@ XF_FN void xfacc_fma(xfacc<W>& a, const xf<W>& x, const xf<W>& y, bool neg = fal
   const int d = a.E - (x.e + y.e + 1);
   shr_words<W + 1>(h, z ? 64 * (W + 1) : d, r);
   const uint64_t mask = ((x.s ^ y.s) != 0) != neg ? ~0ULL : 0ULL;
-  uint64_t c = mask & 1ULL;
+  // a.w += (r, sign-extended to W+2 words, negated in two's complement
+  // when mask is set)
+  uint64_t yv[W + 2];
 #pragma unroll
-  for (int i = 0; i <= W; ++i) {
-    const uint64_t yv = r[i] ^ mask;
-    const uint64_t u = a.w[i] + yv;
-    const uint64_t c1 = u < a.w[i];
-    const uint64_t v = u + c;
-    c = c1 | (v < u);
-    a.w[i] = v;
-  }
-  a.w[W + 1] += mask + c;
+  for (int i = 0; i <= W; ++i) yv[i] = r[i] ^ mask;
+  yv[W + 1] = mask;
+  add_words<W + 2>(a.w, yv, mask & 1ULL);
 }
 
 template <int W>
@@ -468,17 +645,11 @@ XF_FN void xf_from_md(const double (&a)[K], xf<W>& r) {
     uint64_t ys[W + 1];
     shr_guard<W>(top, E0 - El, ys);
     const uint64_t mask = ((bl >> 63) ^ s0) ? ~0ULL : 0ULL;
-    uint64_t c = mask & 1ULL;
+    uint64_t yv[W + 2];
 #pragma unroll
-    for (int i = 0; i <= W; ++i) {
-      const uint64_t yv = ys[i] ^ mask;
-      const uint64_t u = g[i] + yv;
-      const uint64_t c1 = u < g[i];
-      const uint64_t v = u + c;
-      c = c1 | (v < u);
-      g[i] = v;
-    }
-    g[W + 1] += mask + c;
+    for (int i = 0; i <= W; ++i) yv[i] = ys[i] ^ mask;
+    yv[W + 1] = mask;
+    add_words<W + 2>(g, yv, mask & 1ULL);
   }
   uint64_t h[W + 1];
   const bool carry = g[W + 1] != 0ULL;

@@ -55,9 +55,9 @@ INT_LANES_PER_CLK_PER_SM = 64
 INT_PEAK_OPS = NUM_SMS * INT_LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
 # Integer thread instructions per md multiply-add in integer limbs, by
 # limbs (real data): measured with ncu on ed_kernel at the quad double
-# workload, 2.976e9 integer instructions for 12 104 x 528 = 6.39e6
+# workload, 2.591e9 integer instructions for 12 104 x 528 = 6.39e6
 # multiply-adds (operand conversions and the accumulator included).
-XF_INT_OPS_PER_FMA = {4: 466.0}
+XF_INT_OPS_PER_FMA = {4: 405.5}
 
 METRIC = "Newton steps/s (qd, n=64, d=31)"
 
@@ -100,7 +100,11 @@ def parse():
 # DRAM bytes (read + write) per launch of the phase's main kernel from one ncu
 # capture of the unchanged kernels (profiles/ncu_qr_ed_fsub_qd-real-n64-d31.md);
 # absent entries report null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("qd-real-n64-d31", "qr"): 603904 + 8448,
+    ("qd-real-n64-d31", "evaluate"): 1294848,
+    ("qd-real-n64-d31", "forward"): 4622592 + 42368,
+}
 
 
 def dist_info():

@@ -126,7 +126,9 @@ XF_FN uint64_t fshl(uint64_t lo, uint64_t hi, int b) {
 // Carry chains.  On the device they are single inline-PTX blocks of add.cc /
 // addc.cc, so the carry travels in the condition code from word to word
 // (one add per word) instead of being rebuilt from unsigned compares; the
-// condition code lives only inside each block.
+// condition code lives only inside each block.  The first add of a block,
+// cin + (2^64 - 1), sets the carry flag to cin (0 or 1); the last one reads
+// the carry out of the top word.
 #if defined(__CUDACC__)
 template <int N>
 struct addc_ptx;

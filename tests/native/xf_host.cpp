@@ -93,3 +93,40 @@ extern "C" int xf_host_conv(int K, int D, const double* a, const double* b, doub
   }
   return 1;
 }
+
+// a + b + cin over N 64-bit words (a, b, out: N words, least significant
+// first); returns the carry out, or -1 for an unsupported N.
+template <int N>
+static int addw(const uint64_t* a, const uint64_t* b, uint64_t cin, uint64_t* out) {
+  uint64_t x[N], y[N];
+  for (int i = 0; i < N; ++i) {
+    x[i] = a[i];
+    y[i] = b[i];
+  }
+  const uint64_t c = add_words<N>(x, y, cin);
+  for (int i = 0; i < N; ++i) out[i] = x[i];
+  return (int)c;
+}
+
+extern "C" int xf_host_add_words(int N, const uint64_t* a, const uint64_t* b, uint64_t cin, uint64_t* out) {
+  switch (N) {
+    case 1: return addw<1>(a, b, cin, out);
+    case 2: return addw<2>(a, b, cin, out);
+    case 3: return addw<3>(a, b, cin, out);
+    case 4: return addw<4>(a, b, cin, out);
+    case 5: return addw<5>(a, b, cin, out);
+    case 6: return addw<6>(a, b, cin, out);
+    case 7: return addw<7>(a, b, cin, out);
+    case 8: return addw<8>(a, b, cin, out);
+    case 9: return addw<9>(a, b, cin, out);
+  }
+  return -1;
+}
+
+// (c:s) += v for each v of vals[count]; returns s, c in out[0], out[1].
+extern "C" void xf_host_add_count(int count, const uint64_t* vals, uint64_t s0, uint64_t c0, uint64_t* out) {
+  uint64_t s = s0, c = c0;
+  for (int i = 0; i < count; ++i) add_count(s, c, vals[i]);
+  out[0] = s;
+  out[1] = c;
+}

@@ -187,3 +187,55 @@ def test_fixed_point_convolution(lib, K, D):
         got = ex.md_to_fr(out[k])
         _nonoverlapping(out[k])
         assert abs(got - want) <= Fr(2) ** (12 - 64 * W) * mag, (k, float(got - want), float(mag))
+
+
+def _words(v, N):
+    return np.array([(v >> (64 * i)) & (2**64 - 1) for i in range(N)], dtype=np.uint64)
+
+
+def _value(w):
+    return sum(int(x) << (64 * i) for i, x in enumerate(w))
+
+
+@pytest.mark.parametrize("N", range(1, 10))
+def test_multiword_carry_chain(lib, N):
+    """add_words: a + b + cin modulo 2^(64N) with the carry out, against
+    Python integers, on carries that run through every word (all-ones
+    operands, a carry-in into 2^(64N) - 1) and on random words."""
+    P = ctypes.POINTER(ctypes.c_uint64)
+    lib.xf_host_add_words.restype = ctypes.c_int
+    lib.xf_host_add_words.argtypes = [ctypes.c_int, P, P, ctypes.c_uint64, P]
+    M = 2**(64 * N)
+    rng = np.random.default_rng(700 + N)
+    cases = [(M - 1, 0, 1), (M - 1, M - 1, 1), (M - 1, M - 1, 0), (0, 0, 1), (M - 1, 1, 0),
+             (2**63, 2**63, 0), (M // 2, M // 2, 1)]
+    for _ in range(200):
+        a = int.from_bytes(rng.bytes(8 * N), "little")
+        b = int.from_bytes(rng.bytes(8 * N), "little")
+        # words that are all ones or zero in places make long carry runs
+        if rng.random() < 0.5:
+            a |= sum((2**64 - 1) << (64 * i) for i in range(N) if rng.random() < 0.5)
+        cases.append((a, b, int(rng.integers(0, 2))))
+    for a, b, cin in cases:
+        wa, wb = _words(a, N), _words(b, N)
+        out = np.zeros(N, dtype=np.uint64)
+        c = lib.xf_host_add_words(N, wa.ctypes.data_as(P), wb.ctypes.data_as(P), cin, out.ctypes.data_as(P))
+        total = a + b + cin
+        assert _value(out) == total % M and c == total // M, (hex(a), hex(b), cin)
+
+
+def test_column_sum_with_counted_carries(lib):
+    """add_count: s plus many words, the carries counted in c, equals the
+    exact sum as the two-word number c:s."""
+    P = ctypes.POINTER(ctypes.c_uint64)
+    lib.xf_host_add_count.restype = None
+    lib.xf_host_add_count.argtypes = [ctypes.c_int, P, ctypes.c_uint64, ctypes.c_uint64, P]
+    rng = np.random.default_rng(731)
+    for count in (0, 1, 2, 15, 16, 17):
+        for s0 in (0, 2**64 - 1, int(rng.integers(0, 2**63))):
+            vals = np.array([2**64 - 1] * (count // 2) + [int(x) for x in rng.integers(0, 2**63, count - count // 2)],
+                            dtype=np.uint64)
+            out = np.zeros(2, dtype=np.uint64)
+            lib.xf_host_add_count(count, vals.ctypes.data_as(P), s0, 5, out.ctypes.data_as(P))
+            total = s0 + 5 * 2**64 + sum(int(v) for v in vals)
+            assert int(out[0]) + (int(out[1]) << 64) == total

@@ -294,6 +294,24 @@ mdn_status mdn_evaluate_static(int limbs, int is_complex, int n, int degree, int
                                const double* coeff, const double* const_term, const double* x, double* f_out,
                                void* cuda_stream);
 
+/* The product schedule that the evaluation runs for one monomial of k
+ * variables (Section 5.1: the three columns of forward products
+ * F_j = F_{j-1} x_j, backward products B_j = B_{j-1} x_{k-j+1} and cross
+ * products F_{p} B_{k-1-p}; the coefficient series c enters as F_0, so a
+ * monomial with k >= 2 costs 3k-3 products, the paper's 3k-5 plus two).
+ * Host only: no CUDA call, no device memory; it exposes the table that
+ * mdn_load_system uploads so that host tests can execute it symbolically.
+ *   k: 1..4096 variables; groups: 1..32 products that one warp runs at once.
+ *   *n_waves receives the number of waves.  With ops non-NULL, ops receives
+ *   n_waves * groups records of four int32 (op, destination, a, b): op 0 is
+ *   an idle group, 1 a truncated product dst = a * b, 2 a copy dst = a; a
+ *   slot is kind << 16 | index with kind 1 the coefficient c, 2 the input
+ *   x_{index+1} (position in the monomial), 3 F_index, 4 B_index, 5 the
+ *   value and 6 the partial with respect to position index.  capacity is the
+ *   number of records ops holds; fewer than needed returns MDN_EINVAL.
+ * Products of one wave read only slots written by earlier waves. */
+mdn_status mdn_ed_schedule(int k, int groups, int32_t* ops, int capacity, int* n_waves);
+
 /* Synchronise the context's stream and return the device status as an
  * mdn_status (MDN_OK when no device condition was raised). */
 mdn_status mdn_status_word(mdn_ctx* ctx);

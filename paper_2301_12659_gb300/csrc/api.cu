@@ -1061,6 +1061,23 @@ mdn_status mdn_profile(mdn_ctx* ctx, int enable, double* ms_out, int64_t* launch
 
 const char* mdn_last_error(const mdn_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+mdn_status mdn_ed_schedule(int k, int groups, int32_t* ops, int capacity, int* n_waves) {
+  if (k < 1 || k > 4096 || groups < 1 || groups > 32 || !n_waves || capacity < 0) return MDN_EINVAL;
+  std::vector<int4> w;
+  int nw = 0;
+  build_schedule(k, groups, w, nw);
+  *n_waves = nw;
+  if (!ops) return MDN_OK;
+  if ((size_t)capacity < w.size()) return MDN_EINVAL;
+  for (size_t i = 0; i < w.size(); ++i) {
+    ops[4 * i] = w[i].x;
+    ops[4 * i + 1] = w[i].y;
+    ops[4 * i + 2] = w[i].z;
+    ops[4 * i + 3] = w[i].w;
+  }
+  return MDN_OK;
+}
+
 void mdn_destroy(mdn_ctx* ctx) {
   if (!ctx) return;
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);

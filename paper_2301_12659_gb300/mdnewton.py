@@ -31,7 +31,7 @@ MDN_MAX_DEGREE = 63
 EXPORTS = ("mdn_create", "mdn_workspace_bytes", "mdn_load_system", "mdn_set_series", "mdn_newton",
            "mdn_get_series", "mdn_get_residual", "mdn_evaluate", "mdn_solve", "mdn_profile",
            "mdn_status_word", "mdn_last_error", "mdn_destroy", "mdn_evaluate_static", "mdn_set_late_updates", "mdn_adjoint", "mdn_fabry_loss", "mdn_set_residual_rows", "mdn_set_stagger",
-           "mdn_batch_create", "mdn_batch_workspace_bytes", "mdn_batch_load", "mdn_batch_evaluate",
+           "mdn_ed_schedule", "mdn_batch_create", "mdn_batch_workspace_bytes", "mdn_batch_load", "mdn_batch_evaluate",
            "mdn_batch_solve", "mdn_batch_tiles", "mdn_batch_last_error", "mdn_batch_destroy")
 BATCH_CONVERGED, BATCH_SINGULAR, BATCH_NONFINITE = 1, 2, 4
 MDN_NUM_PHASES = 5
@@ -84,6 +84,7 @@ def load(path: str = None) -> ctypes.CDLL:
     L.mdn_batch_last_error.restype = ctypes.c_char_p
     L.mdn_batch_destroy.argtypes = [P]
     L.mdn_evaluate_static.argtypes = [I, I, I, I, I, I, P, P, P, P, P, P, P, P]
+    L.mdn_ed_schedule.argtypes = [I, I, P, I, ctypes.POINTER(I)]
     L.mdn_last_error.argtypes = [P]
     L.mdn_last_error.restype = ctypes.c_char_p
     L.mdn_destroy.argtypes = [P]
@@ -177,6 +178,23 @@ def mdn_profile(ctx, enable: int):
     st = load().mdn_profile(ctx, int(enable), ms.ctypes.data_as(ctypes.c_void_p),
                             launches.ctypes.data_as(ctypes.c_void_p))
     return st, ms, launches
+
+
+def mdn_ed_schedule(k, groups):
+    """The evaluation's product schedule for a monomial of k variables with
+    `groups` products per warp wave: an int32 array [waves][groups][4] of
+    (op, destination, a, b) records (host only; see include/mdnewton.h)."""
+    L = load()
+    nw = ctypes.c_int(0)
+    st = L.mdn_ed_schedule(int(k), int(groups), None, 0, ctypes.byref(nw))
+    if st != MDN_OK:
+        raise ValueError(f"mdn_ed_schedule({k}, {groups}) returned {st}")
+    ops = np.zeros((nw.value, int(groups), 4), dtype=np.int32)
+    st = L.mdn_ed_schedule(int(k), int(groups), ops.ctypes.data_as(ctypes.c_void_p), nw.value * int(groups),
+                           ctypes.byref(nw))
+    if st != MDN_OK:
+        raise ValueError(f"mdn_ed_schedule({k}, {groups}) returned {st}")
+    return ops
 
 
 def mdn_evaluate_static(limbs, is_complex, n, degree, n_monomials, n_var_refs, eq_of_monomial, var_ptr, var_idx,

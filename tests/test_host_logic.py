@@ -144,3 +144,38 @@ def test_ed_schedule_of_the_four_variable_example():
     ])
     assert prods == expect
     assert ops.shape[0] == 4
+
+
+def _bench(args, env_extra=None):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], capture_output=True, text=True,
+                       timeout=300, env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_reference_arm_prints_one_line_of_the_contract():
+    """bench.py --impl reference times the CPU oracle on the workload's
+    metric and prints one JSON line with the reference arm's keys."""
+    lines = _bench(["--impl", "reference", "--config", "dd-real-n8-d15", "--steps", "3", "--warmup", "3"])
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["metric"] == "Newton steps/s (dd, n=8, d=15)"
+    assert d["unit"] == "steps/s" and d["higher_is_better"] is True and d["steps"] == 3 and d["warmup"] == 3
+    assert d["value"] > 0 and d["vs_baseline"] is None and d["config"]["workload"] == "dd-real-n8-d15"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under torchrun the ranks other than 0 exit without work or output."""
+    lines = _bench(["--impl", "reference", "--config", "dd-real-n8-d15", "--steps", "3", "--warmup", "3"],
+                   {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert lines == []

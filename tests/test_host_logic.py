@@ -179,3 +179,31 @@ def test_reference_arm_runs_on_rank_zero_only():
     lines = _bench(["--impl", "reference", "--config", "dd-real-n8-d15", "--steps", "3", "--warmup", "3"],
                    {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert lines == []
+
+
+def test_autotuner_cache_is_keyed_by_gpu_and_size_classes(tmp_path, monkeypatch):
+    """batch_tiles reads the cache entry of (GPU, limbs, real/complex, size
+    classes) when present, and otherwise tunes once and stores the choice."""
+    cfg = wl.small_config(4, 1, n=4, d=7, mono_per_eq=2, kmin=1, kmax=3, index=960)
+    cfg2 = wl.small_config(4, 1, n=8, d=7, mono_per_eq=2, kmin=1, kmax=3, index=961)
+    items = [wl.planted_system(cfg), wl.planted_system(cfg2), wl.planted_system(cfg)]
+    assert autotune.signature([s for s, _, _ in items]) == "K4C1|4x7,8x7"
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tiles.json"))
+    monkeypatch.setattr(autotune, "_gpu_name", lambda: "GPU-A")
+    calls = []
+
+    def fake_tune(its, max_steps, tol, sample=4096, candidates=None, log=None):
+        calls.append(len(its))
+        return 256, 1, [{"threads": 256, "blocks_per_sm": 1, "ms": 1.0}]
+
+    monkeypatch.setattr(autotune, "tune", fake_tune)
+    t, b, e = autotune.batch_tiles(items, 12, 1e-50)
+    assert (t, b) == (256, 1) and calls == [3]
+    t, b, e = autotune.batch_tiles(items, 12, 1e-50)  # cached: no second tuning
+    assert (t, b) == (256, 1) and calls == [3]
+    monkeypatch.setattr(autotune, "_gpu_name", lambda: "GPU-B")  # another GPU tunes again
+    autotune.batch_tiles(items, 12, 1e-50)
+    assert calls == [3, 3]
+    import json
+    keys = sorted(json.load(open(tmp_path / "tiles.json")))
+    assert keys == ["GPU-A|K4C1|4x7,8x7", "GPU-B|K4C1|4x7,8x7"]

@@ -115,3 +115,56 @@ def test_converged_update_vanishes():
     x2, hist = oracle.newton(s, x, 1)
     assert hist[0, 2] <= 1e-27 and hist[0, 0] <= 1e-27
     assert np.max(mt.series_rel_error(x2, x)) <= 1e-28
+
+
+@pytest.mark.parametrize("K,C,D", [(2, 1, 4), (4, 1, 3), (4, 2, 3), (8, 1, 3), (8, 2, 2)])
+def test_one_newton_step_exact(K, C, D):
+    """One step of the Section 2 pseudo code in exact rationals: f and the
+    Jacobian series A_j = [t^j] df/dx at x(t), the block lower triangular
+    Toeplitz solve of A dx = -f, and x + dx.  The oracle's step (which
+    follows the same steps with its own QR and forward substitution) must
+    agree to the md rounding level, with powers among the monomials, a full
+    start series (every coefficient nonzero) and the history columns
+    ||f(x)||_1 and ||dx||_1 of its leading doubles."""
+    n = 3
+    # monomial variables; repeated indices are powers
+    mons = [(0, [0, 1]), (0, [0, 0, 2]), (0, [0]), (1, [1, 2]), (1, [1]), (1, [2, 2]),
+            (2, [2, 0]), (2, [2]), (2, [1, 1, 0])]
+    eq = np.array([e for e, _ in mons], dtype=np.int32)
+    vptr = np.cumsum([0] + [len(v) for _, v in mons]).astype(np.int32)
+    vidx = np.array([q for _, v in mons for q in v], dtype=np.int32)
+    M = len(mons)
+    coeff = wl.random_md((M, D), K, C, 880 + K + C)
+    for m, (e, v) in enumerate(mons):
+        if v == [e]:
+            coeff[0, 0, m, 0] += 4.0  # a dominant diagonal keeps A_0 well conditioned
+    s = wl.System(K, C, n, D - 1, eq, vptr, vidx, coeff, wl.random_md((n, D), K, C, 890 + K))
+    x0 = wl.random_md((n, D), K, C, 900 + K + C)
+
+    x1, hist = oracle.newton(s, x0, 1)
+
+    fx = ex.arr_to_fr(x0)
+    x = [[fx[i, k] for k in range(D)] for i in range(n)]
+    f = ex.system_fr(s, x)
+    fc = ex.arr_to_fr(coeff)
+    A = [[[ex.zero(C) for _ in range(n)] for _ in range(n)] for _ in range(D)]
+    for m, (e, v) in enumerate(mons):
+        for q in range(len(v)):  # d/dx_{v[q]}: the product of the other factors
+            p = [fc[m, k] for k in range(D)]
+            for r, u in enumerate(v):
+                if r != q:
+                    p = ex.series_mul(p, x[u], D, C)
+            for j in range(D):
+                A[j][e][v[q]] = ex.add(A[j][e][v[q]], p[j])
+    neg_f = [[ex.sub(ex.zero(C), f[i][k]) for k in range(D)] for i in range(n)]
+    dx = ex.toeplitz_solve_fr(A, neg_f, C)
+    expect = np.empty((n, D), dtype=object)
+    for i in range(n):
+        for k in range(D):
+            expect[i, k] = ex.add(x[i][k], dx[i][k])
+    assert ex.worst_rel_log2(x1, expect, floor=1.0) <= -51 * K + 14
+
+    norm_f = sum(ex.absf(f[i][k]) for i in range(n) for k in range(D))
+    norm_dx = sum(ex.absf(dx[i][k]) for i in range(n) for k in range(D))
+    assert abs(hist[0, 0] - norm_f) <= 1e-13 * norm_f
+    assert abs(hist[0, 2] - norm_dx) <= 1e-13 * norm_dx

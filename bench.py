@@ -55,9 +55,9 @@ INT_LANES_PER_CLK_PER_SM = 64
 INT_PEAK_OPS = NUM_SMS * INT_LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
 # Integer thread instructions per md multiply-add in integer limbs, by
 # limbs (real data): measured with ncu on ed_kernel at the quad double
-# workload, 2.591e9 integer instructions for 12 104 x 528 = 6.39e6
+# workload, 2.591e9 integer instructions for 12 070 x 528 = 6.37e6
 # multiply-adds (operand conversions and the accumulator included).
-XF_INT_OPS_PER_FMA = {4: 405.5}
+XF_INT_OPS_PER_FMA = {4: 406.6}
 
 METRIC = "Newton steps/s (qd, n=64, d=31)"
 

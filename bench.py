@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--config", default="qd-real-n64-d31", choices=sorted(wl.CONFIGS))
     ap.add_argument("--e2e-solves", type=int, default=5)
     ap.add_argument("--cpu-sample-steps", type=int, default=14)
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="host threads of the CPU oracle (0: all cores; 1 times it single-threaded)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", default="on", choices=["on", "off"],
                     help="also time the batched workload (4096 quad double systems) and the same systems one by one")
@@ -178,9 +180,12 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # reference arm and CPU baseline: the CPU oracle
 # ---------------------------------------------------------------------------
-def oracle_sample(cfg, nsteps):
-    """Time `nsteps` oracle Newton steps on the workload (host cores)."""
+def oracle_sample(cfg, nsteps, threads=0):
+    """Time `nsteps` oracle Newton steps on the workload (host cores; all of
+    them unless `threads` > 0)."""
     from oracle import oracle
+    if threads > 0:
+        oracle.set_threads(threads)
     s, xstar, x0 = wl.planted_system(cfg)
     s.cst = oracle.planted_constant(s, xstar)
     t0 = time.perf_counter()
@@ -194,6 +199,8 @@ def run_reference(args, cfg):
     if rank != 0:
         return
     from oracle import oracle
+    if args.cpu_threads > 0:
+        oracle.set_threads(args.cpu_threads)
     s, xstar, x0 = wl.planted_system(cfg)
     s.cst = oracle.planted_constant(s, xstar)
     x = x0
@@ -539,7 +546,7 @@ def run_ours(args, cfg):
     if args.adjoint == "on":
         line["adjoint"] = run_adjoint(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, cores = oracle_sample(cfg, args.cpu_sample_steps)
+        dt, cores = oracle_sample(cfg, args.cpu_sample_steps, args.cpu_threads)
         line["cpu_baseline"] = {"value": args.cpu_sample_steps / dt, "unit": "steps/s", "cores": cores,
                                 "kind": "oracle",
                                 "sample": f"{args.cpu_sample_steps} oracle Newton steps from the start series"}

@@ -207,3 +207,21 @@ def test_autotuner_cache_is_keyed_by_gpu_and_size_classes(tmp_path, monkeypatch)
     import json
     keys = sorted(json.load(open(tmp_path / "tiles.json")))
     assert keys == ["GPU-A|K4C1|4x7,8x7", "GPU-B|K4C1|4x7,8x7"]
+
+
+def test_cpu_baseline_thread_count():
+    """The CPU baseline leg times the oracle on all host cores by default
+    and on the number of threads asked for otherwise; it reports the count
+    it used."""
+    import bench
+    from oracle import oracle
+    cfg = wl.CONFIGS["dd-real-n8-d15"]
+    all_cores = oracle.get_threads()
+    try:
+        dt, cores = bench.oracle_sample(cfg, 2, threads=1)
+        assert cores == 1 and dt > 0
+    finally:
+        oracle.set_threads(all_cores)
+    lines = _bench(["--impl", "reference", "--config", "dd-real-n8-d15", "--steps", "3", "--warmup", "3",
+                    "--cpu-threads", "1"])
+    assert lines[0]["cpu_baseline"]["cores"] == 1

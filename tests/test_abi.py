@@ -56,3 +56,11 @@ def test_product_path_never_imports_the_oracle():
                         assert (node.module or "").split(".")[0] != "oracle", path
             elif f.endswith((".cu", ".cuh", ".h", ".cpp")):
                 assert "mdoracle" not in open(path).read(), path
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without the built library the binding raises: there is no fallback."""
+    from paper_2301_12659_gb300 import mdnewton
+    monkeypatch.setattr(mdnewton, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        mdnewton.load(str(tmp_path / "libmdnewton-missing.so"))

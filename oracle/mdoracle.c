@@ -689,14 +689,26 @@ static double norm1(const mdc *v, long N, int C) {
     return s;
 }
 
-/* ||B - T DX||_1 with T the block Toeplitz matrix, every entry in md.  The
-   entries' magnitudes are summed in row-major order after the parallel loop,
-   so the reported norm does not depend on the thread count. */
-static double toeplitz_residual(int K, int C, int n, int d, const mdc *A, const mdc *B, const mdc *DX) {
+/* ||B - T DX||_1 with T the block Toeplitz matrix, every entry in md:
+   entry (i, k) of the residual is b_k[i] - sum_{j=0..k} (A_j dx_{k-j})[i]
+   (Eq. (eqToeplitz)), its exact value rounded once.  R (may be NULL) receives
+   the md residual series.  With rows != NULL only the `count` rows listed
+   enter the norm, scaled by n / count (the sampled monitor of Section 5.4).
+   The entries' magnitudes are summed in row-major order after the parallel
+   loop, so the reported norm does not depend on the thread count. */
+static double toeplitz_residual_rows(int K, int C, int n, int d, const mdc *A, const mdc *B, const mdc *DX,
+                                     mdc *R, const int32_t *rows, int count) {
     const int D = d + 1;
-    double *mag = (double *)malloc(sizeof(double) * (size_t)n * D);
+    double *mag = (double *)calloc((size_t)n * D, sizeof(double));
+    char *in = (char *)calloc((size_t)n, 1);
+    if (rows) {
+        for (int q = 0; q < count; ++q) in[rows[q]] = 1;
+    } else {
+        memset(in, 1, (size_t)n);
+    }
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
+        if (!in[i] && !R) continue;
         cacc_t *t = (cacc_t *)malloc(sizeof(cacc_t));
         for (int k = 0; k < D; ++k) {
             mdc r;
@@ -706,14 +718,20 @@ static double toeplitz_residual(int K, int C, int n, int d, const mdc *A, const 
                 for (int l = 0; l < n; ++l)
                     cacc_add_prod(t, &A[((size_t)j * n + i) * n + l], &DX[(size_t)l * D + (k - j)], K, C, -1.0);
             cacc_round(t, K, C, &r);
-            mag[(size_t)i * D + k] = norm1(&r, 1, C);
+            if (R) R[(size_t)i * D + k] = r;
+            if (in[i]) mag[(size_t)i * D + k] = norm1(&r, 1, C);
         }
         free(t);
     }
     double total = 0.0;
     for (long e = 0; e < (long)n * D; ++e) total += mag[e];
     free(mag);
-    return total;
+    free(in);
+    return rows ? total * ((double)n / count) : total;
+}
+
+static double toeplitz_residual(int K, int C, int n, int d, const mdc *A, const mdc *B, const mdc *DX) {
+    return toeplitz_residual_rows(K, C, n, d, A, B, DX, NULL, NULL, 0);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -890,6 +908,33 @@ int orc_solve_late(int K, int C, int n, int d, const double *A, const double *b,
     free(B);
     free(AA);
     return rc;
+}
+
+int orc_toeplitz_residual(int K, int C, int n, int d, const double *A, const double *b, const double *dx,
+                          const int32_t *rows, int count, double *r, double *norm) {
+    if (check_kc(K, C) || n < 1 || d < 0 || !norm) return ORC_EINVAL;
+    if (rows) {
+        if (count < 1 || count > n) return ORC_EINVAL;
+        for (int q = 0; q < count; ++q)
+            if (rows[q] < 0 || rows[q] >= n) return ORC_EINVAL;
+    }
+    const long D = d + 1;
+    mdc *AA = (mdc *)malloc(sizeof(mdc) * (size_t)D * n * n);
+    mdc *B = (mdc *)malloc(sizeof(mdc) * (size_t)n * D);
+    mdc *X = (mdc *)malloc(sizeof(mdc) * (size_t)n * D);
+    mdc *R = r ? (mdc *)malloc(sizeof(mdc) * (size_t)n * D) : NULL;
+    soa_to_mdc(A, K, C, D * n * n, AA);
+    soa_to_mdc(b, K, C, (long)n * D, B);
+    soa_to_mdc(dx, K, C, (long)n * D, X);
+    *norm = toeplitz_residual_rows(K, C, n, d, AA, B, X, R, rows, count);
+    if (R) {
+        mdc_to_soa(R, K, C, (long)n * D, r);
+        free(R);
+    }
+    free(X);
+    free(B);
+    free(AA);
+    return ORC_OK;
 }
 
 int orc_newton(int K, int C, int n, int d, int M, const int32_t *eq, const int32_t *vptr,

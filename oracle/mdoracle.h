@@ -72,6 +72,15 @@ int orc_solve(int K, int C, int n, int d, const double *A, const double *b, doub
 int orc_solve_late(int K, int C, int n, int d, const double *A, const double *b, int late_stage, int late_K,
                    double *dx);
 
+/* Residual of the block lower triangular Toeplitz system of Eq. (eqToeplitz)
+ * (the residuals of Sections 5.4 and 6): r_k = b_k - sum_{j=0..k} A_j dx_{k-j},
+ * each entry its exact value rounded once to K limbs, into r [K][C][n][d+1]
+ * (may be NULL), and *norm = its 1-norm of leading doubles (|re| or hypot).
+ * With rows != NULL only the `count` distinct rows listed enter the norm,
+ * scaled by n / count (the sampled monitor of Section 5.4). */
+int orc_toeplitz_residual(int K, int C, int n, int d, const double *A, const double *b, const double *dx,
+                          const int32_t *rows, int count, double *r, double *norm);
+
 /* Newton's method on power series (Section 2 pseudo code): `steps` iterations
  * from x0, no early exit.  x_out [K][C][n][d+1]; hist [steps][3] holds per
  * step ||f(x)||_1 before the update, the monitor ||b - A dx||_1 and ||dx||_1

@@ -71,10 +71,11 @@ def lib():
             L.orc_fabry_loss.argtypes = [i, i, i, P, P, P]
             L.orc_newton_staggered.argtypes = [i, i, i, i, i, P, P, P, P, P, P, i, i, P, P, P]
             L.orc_adjoint.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P]
+            L.orc_toeplitz_residual.argtypes = [i, i, i, i, P, P, P, P, i, P, P]
             for name in ("orc_md_binary", "orc_md_sqrt", "orc_series_mul", "orc_evaluate",
                          "orc_planted_constant", "orc_qr", "orc_solve", "orc_newton", "orc_solve_late",
                          "orc_newton_late", "orc_fabry_loss", "orc_adjoint",
-                         "orc_newton_staggered"):
+                         "orc_newton_staggered", "orc_toeplitz_residual"):
                 getattr(L, name).restype = i
             _lib = L
     return _lib
@@ -185,6 +186,20 @@ def solve(A, b, late=None) -> np.ndarray:
     else:
         _check(lib().orc_solve_late(K, C, n, D - 1, _p(A), _p(b), int(late[0]), int(late[1]), _p(dx)), "solve")
     return dx
+
+
+def toeplitz_residual(A, b, dx, rows=None):
+    """Residual r_k = b_k - sum_{j<=k} A_j dx_{k-j} of the block Toeplitz
+    system (md values [K,C,n,d+1]) and its 1-norm of leading doubles; with
+    `rows`, the norm over those rows scaled by n / len(rows)."""
+    A, b, dx = _f64(A), _f64(b), _f64(dx)
+    K, C, D, n, _ = A.shape
+    r = np.zeros_like(b)
+    norm = np.zeros(1)
+    rr = None if rows is None else _i32(rows)
+    _check(lib().orc_toeplitz_residual(K, C, n, D - 1, _p(A), _p(b), _p(dx), _p(rr),
+                                       0 if rr is None else int(rr.size), _p(r), _p(norm)), "toeplitz_residual")
+    return r, float(norm[0])
 
 
 def newton(sysm, x0, steps: int, late=None):

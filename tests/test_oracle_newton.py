@@ -168,3 +168,57 @@ def test_one_newton_step_exact(K, C, D):
     norm_dx = sum(ex.absf(dx[i][k]) for i in range(n) for k in range(D))
     assert abs(hist[0, 0] - norm_f) <= 1e-13 * norm_f
     assert abs(hist[0, 2] - norm_dx) <= 1e-13 * norm_dx
+
+    # history column 1: the monitor ||b - A dx||_1 of the step (Section 5.4),
+    # b = -f and dx the step's computed (rounded) update, both as the md
+    # values the oracle holds.  Exactly: the residual of the rounded dx, whose
+    # entries are at the md rounding level of the terms A_j dx_{k-j}.
+    f_md, A_md = oracle.evaluate(s, x0)
+    dx_md = oracle.solve(A_md, -f_md)
+    Af, fb, dxf = ex.arr_to_fr(A_md), ex.arr_to_fr(-f_md), ex.arr_to_fr(dx_md)
+    norm_r, size = 0.0, 0.0
+    for i in range(n):
+        for k in range(D):
+            r = fb[i, k]
+            for j in range(k + 1):
+                for l in range(n):
+                    r = ex.sub(r, ex.mul(Af[j, i, l], dxf[l, k - j]))
+                    size += ex.absf(Af[j, i, l]) * ex.absf(dxf[l, k - j])
+            norm_r += ex.absf(r)
+    # the oracle rounds each entry once and sums leading doubles
+    assert abs(hist[0, 1] - norm_r) <= 1e-12 * norm_r + 2.0 ** (-53 * K) * size
+    assert hist[0, 1] <= 2.0 ** (6 - 52 * K) * size
+
+
+@pytest.mark.parametrize("K,C,n,D", [(2, 1, 3, 4), (4, 2, 2, 3), (8, 1, 2, 3)])
+def test_toeplitz_residual_exact(K, C, n, D):
+    """The residual r_k = b_k - sum_{j=0..k} A_j dx_{k-j} of Eq. (eqToeplitz)
+    for an arbitrary (wrong) dx, entry by entry against exact rationals: a
+    dropped j = 0 block, a wrong sign or index, a transposed A_j or a wrong
+    norm all fail.  Its 1-norm of leading doubles, and the sampled form over
+    a subset of rows scaled by n / rows (Section 5.4)."""
+    A = wl.random_md((D, n, n), K, C, 300 + K + C)
+    b = wl.random_md((n, D), K, C, 310 + K + C)
+    dx = wl.random_md((n, D), K, C, 320 + K + C)
+    r, norm = oracle.toeplitz_residual(A, b, dx)
+    Af, bf, xf = ex.arr_to_fr(A), ex.arr_to_fr(b), ex.arr_to_fr(dx)
+    exact = np.empty((n, D), dtype=object)
+    mags = np.zeros((n, D))
+    for i in range(n):
+        for k in range(D):
+            v = bf[i, k]
+            for j in range(k + 1):
+                for l in range(n):
+                    v = ex.sub(v, ex.mul(Af[j, i, l], xf[l, k - j]))
+            exact[i, k] = v
+            mags[i, k] = ex.absf(v)
+    # each entry is its exact value rounded once to K limbs
+    assert ex.worst_rel_log2(r, exact) <= 2 - 52 * K
+    assert abs(norm - mags.sum()) <= 1e-13 * mags.sum()
+    rows = [n - 1]
+    _, part = oracle.toeplitz_residual(A, b, dx, rows=rows)
+    assert abs(part - n * mags[n - 1].sum()) <= 1e-13 * n * mags[n - 1].sum()
+    # the residual of the exact solution is zero up to the md rounding level
+    dx_ok = oracle.solve(A, b)
+    _, small = oracle.toeplitz_residual(A, b, dx_ok)
+    assert small <= 2.0 ** (8 - 52 * K) * (1.0 + norm)

@@ -25,9 +25,8 @@
 //     and 1/sqrt(a) (y += y(1 - ay), y += y(1 - ay^2)/2), started from the
 //     double precision reciprocal / reciprocal square root of the leading
 //     53 bits, each step at the narrowest width that holds the bits it
-//     makes correct: the reciprocal to the md precision (within 2K^2
-//     units of 2^(-53K), the bound of the md operations), the reciprocal
-//     square root to 64W bits;
+//     makes correct: both to a few bits short of 64W, at least 53K + 8
+//     correct bits;
 //   * xf -> md: K times, the leading 53 bits rounded to nearest give a limb
 //     and the exact remainder goes on, so the limbs are nonoverlapping with
 //     |limb_{l+1}| <= ulp(limb_l)/2.
@@ -787,13 +786,14 @@ XF_FN void newton_at(const xf<W>& a, xf<W>& y) {
 }
 // From a 53-bit seed each step doubles the correct bits up to the width it
 // runs at, so the early steps run narrower.  The reciprocal, seeded with the
-// correctly rounded double reciprocal of the leading 53 bits, stops for
-// W <= 4 once about the 53K bits of the md value it serves are correct:
-// widths 1; 1, 2; 2, 4 for W = 1, 2, 4 (53 -> 64; -> 128; -> 106 -> 212
-// bits, less a few for the truncated seed); the octo double width takes one
-// more full-width step (64W bits).  The reciprocal square root (a seed of
-// about 52 bits) starts with a third-order step at 2 words (-> 125 bits)
-// and then doubles: widths 2; 2, 4; 2, 4, 7 for W = 2, 4, 7 (64W bits).
+// correctly rounded double reciprocal of the leading 53 bits (about 52
+// correct bits), runs one step at each width 1, 2, 4, ... up to W: about
+// 62, 122, 242, 440 bits after the steps at 1, 2, 4, 7 words (each step's
+// truncation costs a few bits below its width), at least 53K + 8 bits for
+// the K = 1, 2, 4, 8 limbs that W = 1, 2, 4, 7 serve.  The reciprocal
+// square root (a seed of about 52 bits)
+// starts with a third-order step at 2 words (-> 125 bits) and then doubles:
+// widths 2; 2, 4; 2, 4, 7 for W = 2, 4, 7 (64W bits).
 template <bool RSQRT, int W>
 XF_FN void newton_steps(const xf<W>& a, xf<W>& y) {
   if constexpr (RSQRT && W >= 2) {
@@ -802,21 +802,10 @@ XF_FN void newton_steps(const xf<W>& a, xf<W>& y) {
     if constexpr (W > 4) newton_at<W, true>(a, y);
     return;
   }
-  if constexpr (W == 1) {
-    newton_at<1, RSQRT>(a, y);
-  } else if constexpr (W == 2) {
-    newton_at<1, RSQRT>(a, y);
-    newton_at<2, RSQRT>(a, y);
-  } else if constexpr (W <= 4) {
-    newton_at<2, RSQRT>(a, y);
-    newton_at<W, RSQRT>(a, y);
-    if constexpr (RSQRT) newton_at<W, RSQRT>(a, y);
-  } else {
-    newton_at<2, RSQRT>(a, y);
-    newton_at<4, RSQRT>(a, y);
-    newton_at<W, RSQRT>(a, y);
-    newton_at<W, RSQRT>(a, y);
-  }
+  newton_at<1, RSQRT>(a, y);
+  if constexpr (W >= 2) newton_at<2, RSQRT>(a, y);
+  if constexpr (W >= 4) newton_at<4, RSQRT>(a, y);
+  if constexpr (W > 4) newton_at<W, RSQRT>(a, y);
 }
 
 // r = 1 / a, a nonzero

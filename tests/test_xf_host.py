@@ -132,19 +132,19 @@ def test_zero(lib, K):
 
 @pytest.mark.parametrize("K", [1, 2, 4, 8])
 def test_reciprocal_and_rsqrt(lib, K):
-    """1/a to the md precision (within 2K^2 units of 2^(-53K), the bound of
-    the md operations), 1/sqrt(a) to the xf precision; exact where the
-    result is a short dyadic number."""
+    """1/a and 1/sqrt(a) to the xf precision (2^(8-64W), below the md
+    precision 2^(-53K) by 11 bits or more); rounded to K limbs, within the
+    per-operation contract 2^(-52K) of an md operation (in fact 2^(2-53K));
+    exact where the result is a short dyadic number."""
     W = WORDS[K]
-    md_bound = Fr(2 * K * K) * Fr(2) ** (-53 * K)
     tol = Fr(2) ** (8 - 64 * W)
     for a in _values(K, 100, 950 + K, spread=60):
         A = ex.md_to_fr(a)
         y = ex.md_to_fr(_op(lib, K, "recip", a, extra=True))
-        assert abs(y * A - 1) <= md_bound  # to the md precision
+        assert abs(y * A - 1) <= tol
         yk = _op(lib, K, "recip", a)
         _nonoverlapping(yk)
-        assert abs(ex.md_to_fr(yk) * A - 1) <= md_bound + Fr(2) ** (1 - 53 * K)
+        assert abs(ex.md_to_fr(yk) * A - 1) <= Fr(2) ** (2 - 53 * K)
         if a[0] < 0:  # a positive value
             a, A = -a, -A
         r = ex.md_to_fr(_op(lib, K, "rsqrt", a, extra=True))

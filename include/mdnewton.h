@@ -74,10 +74,15 @@ typedef enum {
 #define MDN_MAX_STEPS 64
 /* Largest truncation degree supported (d+1 <= 64 coefficients). */
 #define MDN_MAX_DEGREE 63
-/* Largest number of equations and unknowns: the QR of A0 keeps its columns
- * and rows in shared memory (a warp per column of A0 and of the identity, a
- * warp per two rows of R^{-1}; all 5n/8 blocks resident, one per SM). */
-#define MDN_MAX_N 192
+/* Largest number of equations and unknowns of a context that solves.  Up to
+ * MDN_MAX_N_DATAFLOW the QR of A0 is one cooperative dataflow launch that
+ * keeps its columns and rows in shared memory (a warp per column of A0 and
+ * of the identity, a warp per two rows of R^{-1}; all 5n/8 blocks resident,
+ * one per SM); above it the QR runs column by column with the columns in
+ * global memory (three launches per reflector, the paper's n = 1024
+ * workloads). */
+#define MDN_MAX_N 1024
+#define MDN_MAX_N_DATAFLOW 192
 /* Largest n of a context that only evaluates (mdn_evaluate, mdn_get_residual;
  * mdn_newton, mdn_solve and mdn_adjoint return MDN_EINVAL above MDN_MAX_N). */
 #define MDN_MAX_N_EVAL 4096
@@ -161,8 +166,7 @@ mdn_status mdn_set_late_updates(mdn_ctx* ctx, int first_stage, int limbs);
  * factorization.  The evaluation, the forward substitution and the update
  * skip the inactive coefficients; the norms of res_hist are over the active
  * ones, and a tolerance stops only at full order.  first_steps = 0 (default)
- * restores the plain method.  mdn_newton returns MDN_EINVAL for staggered
- * orders when a monomial has more than 64 variables. */
+ * restores the plain method. */
 mdn_status mdn_set_stagger(mdn_ctx* ctx, int first_steps);
 
 /* Sampled residual monitor (Section 5.4 suggests the residuals of one or a
@@ -172,6 +176,33 @@ mdn_status mdn_set_stagger(mdn_ctx* ctx, int first_steps);
  * products of the other rows.  count = 0 (or n) restores all rows.  The
  * caller picks the rows (e.g. at random). */
 mdn_status mdn_set_residual_rows(mdn_ctx* ctx, const int32_t* rows, int count);
+
+/* Residual of the block lower triangular Toeplitz system of Eq.
+ * (eqToeplitz) (the residual kernels of Sections 5.4 and 6):
+ *   r_k = b_k - sum_{j=0..k} A_j dx_{k-j},   k = 0..d,
+ * every entry rounded once to K limbs.  A device [K][C][d+1][n][n], b and dx
+ * device [K][C][n][d+1]; r_out (device [K][C][n][d+1]) may be NULL.
+ * *norm_out (host, may be NULL) receives the 1-norm of the leading doubles
+ * of r (|re| or hypot), over the rows set by mdn_set_residual_rows (scaled by
+ * n / count) or all rows.  Enqueued on the context's stream; synchronises to
+ * read the norm.  Overwrites the context's per-entry residual magnitudes
+ * (not the series). */
+mdn_status mdn_residual(mdn_ctx* ctx, const double* A, const double* b, const double* dx, double* r_out,
+                        double* norm_out);
+
+/* out = s * a entry by entry (md multiplication; complex for C = 2): s is
+ * one md value (device [K][C]), a and out device [K][C][count] (out may be
+ * a).  Enqueued on the context's stream.  Used to scale a gradient by an
+ * upstream md factor (the chain rule through an md-valued loss). */
+mdn_status mdn_md_scale(mdn_ctx* ctx, const double* s, const double* a, int64_t count, double* out);
+
+/* Bound of every device wait of the context's dataflow kernels (the QR of A0
+ * and the forward substitution wait on flags and counters that other warps
+ * publish), in nanoseconds of wall time; default 2e9.  A wait that runs out
+ * records MDN_ETIMEOUT in the status word and its kernel returns, so the
+ * synchronising call reports MDN_ETIMEOUT and the context stays usable.
+ * limit_ns >= 1. */
+mdn_status mdn_set_wait_limit_ns(mdn_ctx* ctx, int64_t limit_ns);
 
 /* Adjoint of the converged series (real systems).  At a solution,
  * f(x(c), c) = 0 mod t^{d+1}, so the gradient of a loss L(x) with respect to
@@ -285,8 +316,9 @@ void mdn_batch_destroy(mdn_batch* b);
  * (cudaGetSymbolAddress, with that device current), so that first call should
  * come before any stream capture.  It returns MDN_ETOOLARGE when
  * 8 * (32 + n * 2 * K * C * (d+1)) bytes exceed MDN_STATIC_SCRATCH_BYTES,
- * MDN_EINVAL for bad sizes or an index out of range (checked on the device),
- * and synchronises the stream to read that check.  All calls share the array
+ * MDN_EINVAL for bad sizes or an index out of range (eq_of_monomial,
+ * var_ptr and var_idx, checked on the device); every call ends by
+ * synchronising the stream to read that check.  All calls share the array
  * and it keeps the last call's contents: calls whose kernels overlap on the
  * GPU race.  No cudaMalloc, cudaFree or allocating routine is called. */
 mdn_status mdn_evaluate_static(int limbs, int is_complex, int n, int degree, int n_monomials, int n_var_refs,

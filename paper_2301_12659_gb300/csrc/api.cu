@@ -40,7 +40,8 @@ const KernelTable* kernels_for(int K, int C) {
 // Largest monomial for which the schedules of every product length are built.
 constexpr int STAGGER_KMAX = 64;
 
-// Bounded waits of the dataflow kernels: two seconds of wall time at most.
+// Bounded waits of the dataflow kernels: two seconds of wall time at most by
+// default (mdn_set_wait_limit_ns changes it per context).
 constexpr long long SPIN_LIMIT = 2000000000LL;
 
 __global__ void bump_kernel(unsigned* epoch) { *epoch += 1u; }
@@ -180,7 +181,7 @@ struct Layout {
       o_eq_mon, o_pair_ptr, o_pair_slot, o_occ, o_counter, o_status, o_flags, o_epoch, o_done;
   size_t o_mono_eq, o_adj, o_resmask;
   size_t o_x, o_f, o_dx, o_r, o_out, o_out0, o_scratch, o_A, o_A0b, o_Rm, o_Vm, o_Y, o_Z, o_W, o_xn0, o_tau, o_rinv, o_salpha, o_v0, o_fabs, o_dxabs,
-      o_resabs, o_hist;
+      o_resabs, o_hist, o_rnorm;
 };
 
 struct mdn_ctx {
@@ -195,9 +196,11 @@ struct mdn_ctx {
   std::vector<int4> sched;
   bool loaded = false, has_series = false;
   bool solves = true;  // n small enough for the QR of A0 (else evaluation only)
+  bool large_qr = false;  // the QR runs column by column in global memory
   int late_stage = 1 << 30;  // stages from here form their updates in K/2 limbs
   int res_rows = 0;          // rows of the sampled residual monitor (0: all)
   int stagger_first = 0;     // staggered orders: order-1 steps with a QR each (0: off)
+  long long wait_limit_ns = SPIN_LIMIT;  // bound of every device wait
   std::vector<int> gvals, gidx_of_len;  // lane-group counts of the product lengths 1..D
   const double* coeff = nullptr;
   const double* cst = nullptr;
@@ -416,6 +419,7 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_resabs = take(8 * n * D);
   L.o_resmask = take(4 * n);
   L.o_hist = take(8 * 3 * MDN_MAX_STEPS);
+  L.o_rnorm = take(8 * 3);
   L.total = o;
 }
 
@@ -431,9 +435,13 @@ mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degre
   if (cudaGetDevice(&dev) != cudaSuccess) return MDN_ECUDA;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MDN_ECUDA;
-  // the QR keeps its columns and rows in shared memory with all its blocks
-  // resident, one per SM: beyond that size a context only evaluates
-  const bool solves = n <= MDN_MAX_N && qr_smem_bytes(n, limbs) <= (size_t)QR_SMEM_MAX && qr_blocks_for(n) <= sms;
+  // the dataflow QR keeps its columns and rows in shared memory with all its
+  // blocks resident, one per SM; larger systems (up to MDN_MAX_N) take the
+  // column-by-column QR in global memory; beyond that a context only
+  // evaluates
+  const bool small_qr = n <= MDN_MAX_N_DATAFLOW && qr_smem_bytes(n, limbs) <= (size_t)QR_SMEM_MAX &&
+                        qr_blocks_for(n) <= sms;
+  const bool solves = n <= MDN_MAX_N;
   mdn_ctx* ctx = new (std::nothrow) mdn_ctx();
   if (!ctx) return MDN_EINVAL;
   ctx->K = limbs;
@@ -444,6 +452,7 @@ mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degre
   ctx->kt = kt;
   ctx->num_sms = sms;
   ctx->solves = solves;
+  ctx->large_qr = !small_qr;
   ctx->P = (ctx->D + 1) / 2;  // lanes per product: coefficient pairs (k, D-1-k)
   ctx->G = 32 / ctx->P;       // products in flight per warp
   // one evaluation warp per SM sub-partition: four warps already fill an SM's
@@ -573,6 +582,7 @@ static mdn_status run_a0(mdn_ctx* ctx, const double* x, long long Nx, int xstrid
   a.pair_slot = ctx->at<int>(L.o_pair_slot);
   a.A = A;
   a.NA = NA;
+  a.kmax = ctx->kmax;
   CU(ctx->kt->a0(a, st));
   return MDN_OK;
 }
@@ -586,15 +596,23 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
   const Layout& L = ctx->L;
   const long long D = ctx->D, n = ctx->n;
   if (len <= 0 || len > ctx->D) len = ctx->D;
-  const int gi = ctx->gidx_of_len[len];
-  if (gi < 0) return fail(ctx, MDN_EINVAL, "no product schedule for %d coefficients", len);
+  int gi = ctx->gidx_of_len[len];
+  int G = 32 / ((len + 1) / 2);
+  if (gi < 0) {
+    // monomials too large for a schedule per product length: the schedule of
+    // the full length, whose fewer groups per warp leave lanes idle at this
+    // length (G (len+1)/2 <= 32 still holds)
+    gi = ctx->gidx_of_len[ctx->D];
+    if (gi < 0) return fail(ctx, MDN_EINVAL, "no product schedule for %d coefficients", len);
+    G = ctx->gvals[gi];
+  }
   EdParams e{};
   e.n = ctx->n;
   e.D = ctx->D;
   e.len = len;
   e.M = ctx->M;
   e.P = (len + 1) / 2;
-  e.G = 32 / e.P;
+  e.G = G;
   e.kmax = ctx->kmax;
   e.Smax = ctx->Smax;
   e.Wtot = std::min(blocks * (ED_THREADS / 32), ctx->Wtot);
@@ -669,12 +687,21 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* 
   q.flags = ctx->at<unsigned>(L.o_flags);
   q.epoch = ctx->at<unsigned>(L.o_epoch);
   q.status = ctx->at<int>(L.o_status);
-  q.spin_limit = SPIN_LIMIT;
+  q.spin_limit = ctx->wait_limit_ns;
+  q.large = ctx->large_qr ? 1 : 0;
+  q.Aw = q.Rm;  // the large variant's working columns take the place of R and the reflectors
+  q.Yw = q.Vm;
   CU(ctx->kt->qr(q, st));
   return MDN_OK;
 }
 
-static int qr_blocks(const mdn_ctx* ctx) { return qr_blocks_for(ctx->n); }
+// SMs the QR occupies: the dataflow kernel's blocks, or all of them for the
+// column-by-column variant (which then does not overlap the evaluation)
+static int qr_blocks(const mdn_ctx* ctx) { return ctx->large_qr ? ctx->num_sms : qr_blocks_for(ctx->n); }
+// Kernel launches of A_0 and its QR: two for A_0, the epoch bump, then the
+// dataflow kernel and W, or the column-by-column sequence (initialisation,
+// a pivot and an update launch per column, the back substitution).
+static int qr_launches(const mdn_ctx* ctx) { return 3 + (ctx->large_qr ? 2 * ctx->n + 2 : 2); }
 
 // Forward substitution for dx with right hand side sgn * rhs: stage 0 alone
 // (dx_0 = W r_0, and x_0 + dx_0 into the xnext0 buffer when x is given), the
@@ -716,7 +743,7 @@ static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, l
   u.rdone = ctx->at<unsigned>(L.o_done);
   u.xdone = u.rdone + ctx->D;
   u.status = ctx->at<int>(L.o_status);
-  u.spin_limit = SPIN_LIMIT;
+  u.spin_limit = ctx->wait_limit_ns;
   CU(cudaMemsetAsync(u.rdone, 0, 4 * 2 * (size_t)ctx->D, ctx->stream));
   CU(ctx->kt->stage0(u, ctx->stream));
   if (e0) CU(cudaEventRecord(e0, ctx->stream));
@@ -775,7 +802,7 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
   ph_begin(ctx, MDN_PHASE_QR, qs);
   if ((r = run_a0(ctx, x, n * D, ctx->D, A0b[0], nn, qs)) != MDN_OK) return r;
   if ((r = run_qr(ctx, A0b[0], nn, Wb[0], qs)) != MDN_OK) return r;
-  ph_end(ctx, MDN_PHASE_QR, 5, qs);
+  ph_end(ctx, MDN_PHASE_QR, qr_launches(ctx), qs);
   if (overlap) CU(cudaEventRecord(ctx->ev_join, ctx->side));
   if (ctx->stagger_first > 0) {
     // inactive coefficients contribute nothing to the norms of the step
@@ -799,7 +826,7 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
       ph_begin(ctx, MDN_PHASE_QR, qs);
       if ((r = run_a0(ctx, ctx->at<double>(L.o_xn0), n, 1, A0b[b ^ 1], nn, qs)) != MDN_OK) return r;
       if ((r = run_qr(ctx, A0b[b ^ 1], nn, Wb[b ^ 1], qs)) != MDN_OK) return r;
-      ph_end(ctx, MDN_PHASE_QR, 5, qs);
+      ph_end(ctx, MDN_PHASE_QR, qr_launches(ctx), qs);
       if (overlap) CU(cudaEventRecord(ctx->ev_join, ctx->side));
     }
     UpdParams u{};
@@ -846,8 +873,10 @@ static mdn_status read_status(mdn_ctx* ctx) {
   CU(cudaMemcpyAsync(&st, ctx->at<int>(ctx->L.o_status), 4, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   if (st & MDN_DEV_TIMEOUT) return fail(ctx, MDN_ETIMEOUT, "a bounded device wait timed out");
-  if (st & MDN_DEV_SINGULAR) return fail(ctx, MDN_ESINGULAR, "zero pivot in the Householder QR of A0");
+  // a non-finite value makes the pivots of the QR meaningless too: it is
+  // the cause to report when both are set
   if (st & MDN_DEV_NONFINITE) return fail(ctx, MDN_ENONFINITE, "non-finite value in the series");
+  if (st & MDN_DEV_SINGULAR) return fail(ctx, MDN_ESINGULAR, "zero pivot in the Householder QR of A0");
   return MDN_OK;
 }
 
@@ -858,8 +887,6 @@ mdn_status mdn_newton(mdn_ctx* ctx, int max_steps, double tol, int* steps_done, 
   if (!ctx->has_series) return fail(ctx, MDN_ESTATE, "no series set");
   if (max_steps < 1 || max_steps > MDN_MAX_STEPS) return fail(ctx, MDN_EINVAL, "max_steps out of range");
   if (!ctx->solves) return fail(ctx, MDN_EINVAL, "n = %d > MDN_MAX_N: this context only evaluates", ctx->n);
-  if (ctx->stagger_first > 0 && ctx->kmax > STAGGER_KMAX)
-    return fail(ctx, MDN_EINVAL, "staggered orders need monomials of at most %d variables", STAGGER_KMAX);
   const Layout& L = ctx->L;
   double* hist = ctx->at<double>(L.o_hist);
   CU(cudaMemsetAsync(ctx->at<int>(L.o_status), 0, 4, ctx->stream));
@@ -904,7 +931,7 @@ mdn_status mdn_solve(mdn_ctx* ctx, const double* A, const double* b, double* dx)
   ph_begin(ctx, MDN_PHASE_QR);
   mdn_status r = run_qr(ctx, A, DNN, W, ctx->stream);
   if (r != MDN_OK) return r;
-  ph_end(ctx, MDN_PHASE_QR, 3);
+  ph_end(ctx, MDN_PHASE_QR, qr_launches(ctx) - 2);
   if ((r = run_forward(ctx, A, A, DNN, W, b, +1, dx, nullptr, nullptr, ctx->num_sms)) != MDN_OK) return r;
   return read_status(ctx);
 }
@@ -955,7 +982,7 @@ mdn_status mdn_adjoint(mdn_ctx* ctx, const double* x, const double* g, double* g
   ph_begin(ctx, MDN_PHASE_QR, qs);
   if ((r = run_a0(ctx, x, n * D, ctx->D, A0, n * n, qs)) != MDN_OK) return r;
   if ((r = run_qr(ctx, A0, n * n, W, qs)) != MDN_OK) return r;
-  ph_end(ctx, MDN_PHASE_QR, 5, qs);
+  ph_end(ctx, MDN_PHASE_QR, qr_launches(ctx), qs);
   if (overlap) CU(cudaEventRecord(ctx->ev_join, ctx->side));
   // A_1..A_d (the solve with J^T reads A_0 from the QR's copy)
   if ((r = run_evaluate(ctx, x, f, A, overlap ? ctx->num_sms - qb : ctx->num_sms)) != MDN_OK) return r;
@@ -983,6 +1010,62 @@ mdn_status mdn_adjoint(mdn_ctx* ctx, const double* x, const double* g, double* g
   CU(ctx->kt->adjoint(a, ctx->stream));
   ph_end(ctx, MDN_PHASE_EVALUATE, 1);
   return read_status(ctx);
+}
+
+mdn_status mdn_residual(mdn_ctx* ctx, const double* A, const double* b, const double* dx, double* r_out,
+                        double* norm_out) {
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
+  if (!A || !b || !dx) return fail(ctx, MDN_EINVAL, "null pointer argument");
+  const Layout& L = ctx->L;
+  const long long n = ctx->n, D = ctx->D;
+  ResParams rp{};
+  rp.n = ctx->n;
+  rp.D = ctx->D;
+  rp.A = A;
+  rp.NA = D * n * n;
+  rp.b = b;
+  rp.dx = dx;
+  rp.Nx = n * D;
+  rp.r = r_out;
+  rp.resabs = ctx->at<double>(L.o_resabs);
+  rp.resmask = ctx->res_rows ? ctx->at<int>(L.o_resmask) : nullptr;
+  CU(ctx->kt->residual(rp, ctx->stream));
+  NormParams np{};
+  np.count = n * D;
+  np.fabs = rp.resabs;
+  np.resabs = rp.resabs;
+  np.dxabs = rp.resabs;
+  np.res_scale = ctx->res_rows ? (double)ctx->n / ctx->res_rows : 1.0;
+  np.hist = ctx->at<double>(L.o_rnorm);
+  norms_kernel<<<1, 1024, 0, ctx->stream>>>(np);
+  CU(cudaGetLastError());
+  double h[3];
+  CU(cudaMemcpyAsync(h, np.hist, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (norm_out) *norm_out = h[1];
+  return MDN_OK;
+}
+
+mdn_status mdn_md_scale(mdn_ctx* ctx, const double* s, const double* a, int64_t count, double* out) {
+  if (!ctx) return MDN_EINVAL;
+  if (!ctx->loaded) return fail(ctx, MDN_ESTATE, "no system loaded");
+  if (!s || !a || !out || count < 0) return fail(ctx, MDN_EINVAL, "bad argument");
+  if (count == 0) return MDN_OK;
+  ScaleParams sp{};
+  sp.s = s;
+  sp.a = a;
+  sp.out = out;
+  sp.N = count;
+  CU(ctx->kt->scale(sp, ctx->stream));
+  return MDN_OK;
+}
+
+mdn_status mdn_set_wait_limit_ns(mdn_ctx* ctx, int64_t limit_ns) {
+  if (!ctx) return MDN_EINVAL;
+  if (limit_ns < 1) return fail(ctx, MDN_EINVAL, "the wait limit must be positive");
+  ctx->wait_limit_ns = limit_ns;
+  return MDN_OK;
 }
 
 mdn_status mdn_set_residual_rows(mdn_ctx* ctx, const int32_t* rows, int count) {

@@ -455,6 +455,91 @@ __global__ void a0_partials_kernel(A0Params p) {
   }
   st(p.out0, p.S, (long long)p.mono_sbase[m] + 1 + pos, g);
 }
+// The same partials with a warp per monomial, for monomials of many
+// variables (the direct form costs k-1 products per occurrence, k^2 per
+// monomial): lane l takes the occurrences [l s, (l+1) s), s = ceil(k/32);
+// scans over the lanes of the chunk products give the product of the chunks
+// before and after its own; a forward pass stores c (before) times the
+// prefix within the chunk, a backward pass multiplies in the suffix, about
+// 3k products per monomial.
+template <int K, int C>
+__device__ __forceinline__ void cmd_shfl_up(const cmd<K, C>& v, cmd<K, C>& o, int off) {
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    o.re[l] = __shfl_up_sync(FULL, v.re[l], off);
+    o.im[l] = C == 2 ? __shfl_up_sync(FULL, v.im[l], off) : 0.0;
+  }
+}
+template <int K, int C>
+__device__ __forceinline__ void cmd_shfl_down(const cmd<K, C>& v, cmd<K, C>& o, int off) {
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    o.re[l] = __shfl_down_sync(FULL, v.re[l], off);
+    o.im[l] = C == 2 ? __shfl_down_sync(FULL, v.im[l], off) : 0.0;
+  }
+}
+template <int K, int C>
+__global__ void a0_partials_warp_kernel(A0Params p) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long m = w0; m < p.M; m += nw) {
+    const int vp = p.mono_vp[m], k = p.mono_k[m];
+    const int s = (k + 31) / 32;
+    const int lo = min(k, lane * s), hi = min(k, lo + s);
+    cmd<K, C> one, x, t;
+    cmd_zero(one);
+    one.re[0] = 1.0;
+    cmd<K, C> local = one;  // product of the own chunk
+    for (int q = lo; q < hi; ++q) {
+      ld(p.x, p.Nx, (long long)p.vidx[vp + q] * p.xstride, x);
+      cmd_mul(local, x, t);
+      local = t;
+    }
+    // inclusive scans of the chunk products from the left and from the right
+    cmd<K, C> inc_l = local, inc_r = local, o;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      cmd_shfl_up(inc_l, o, off);
+      if (lane >= off) {
+        cmd_mul(o, inc_l, t);
+        inc_l = t;
+      }
+      cmd_shfl_down(inc_r, o, off);
+      if (lane + off < 32) {
+        cmd_mul(inc_r, o, t);
+        inc_r = t;
+      }
+    }
+    cmd<K, C> before, after;
+    cmd_shfl_up(inc_l, before, 1);
+    cmd_shfl_down(inc_r, after, 1);
+    if (lane == 0) before = one;
+    if (lane == 31) after = one;
+    cmd<K, C> run, c;
+    ld(p.coeff, p.Nc, m * p.D, c);
+    cmd_mul(c, before, t);
+    cmd_mul(t, after, run);
+    const long long slot0 = (long long)p.mono_sbase[m] + 1;
+    for (int q = lo; q < hi; ++q) {  // c * before * after * prefix within the chunk
+      st(p.out0, p.S, slot0 + q, run);
+      ld(p.x, p.Nx, (long long)p.vidx[vp + q] * p.xstride, x);
+      cmd_mul(run, x, t);
+      run = t;
+    }
+    run = one;
+    for (int q = hi - 1; q >= lo; --q) {  // times the suffix within the chunk
+      cmd<K, C> v;
+      ld(p.out0, p.S, slot0 + q, v);
+      cmd_mul(v, run, t);
+      st(p.out0, p.S, slot0 + q, t);
+      ld(p.x, p.Nx, (long long)p.vidx[vp + q] * p.xstride, x);
+      cmd_mul(run, x, t);
+      run = t;
+    }
+  }
+}
+
 template <int K, int C>
 __global__ void a0_assemble_kernel(A0Params p) {
   const long long nn = (long long)p.n * p.n;
@@ -631,6 +716,13 @@ __device__ __forceinline__ int warp_max(int v) {
   for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(FULL, v, off));
   return v;
 }
+// Extra headroom bits of a fixed-point sum of `terms` products beyond the
+// XF_ACC_TERMS that the accumulator's own headroom covers (0 up to 512).
+__device__ __forceinline__ int acc_extra_head(long long terms) {
+  int h = 0;
+  while (((long long)xfn::XF_ACC_TERMS << h) < terms) ++h;
+  return h;
+}
 // sum over the warp of fixed-point accumulators of one scale
 template <int W>
 __device__ __forceinline__ void xfacc_warp_sum(xfn::xfacc<W>& a) {
@@ -689,8 +781,9 @@ __device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const uin
     dot_exp<true, W, C>(xr, xi, yr, yi, er, ei);
   }
   xfn::xfacc<W> ar, ai;
-  xfn::xfacc_init(ar, warp_max(er));
-  if constexpr (C == 2) xfn::xfacc_init(ai, warp_max(ei));
+  const int head = acc_extra_head(C * (n - j));
+  xfn::xfacc_init(ar, warp_max(er) + head);
+  if constexpr (C == 2) xfn::xfacc_init(ai, warp_max(ei) + head);
   for (int i = j + lane; i < n; i += 32) {
     cxf<W, C> x, yi;
     xld<W, C>(p.Vm, p.Nnn, (long long)i * n + j, x);
@@ -712,7 +805,7 @@ __device__ __forceinline__ void qr_norm2(const uint64_t* y, int n, int i0, xfn::
     dot_exp<true, W, C>(yr, yi, yr, yi, er, ei);
   }
   xfn::xfacc<W> ar, ai;
-  xfn::xfacc_init(ar, warp_max(er));
+  xfn::xfacc_init(ar, warp_max(er) + acc_extra_head(C * (n - i0)));
   for (int i = i0 + lane; i < n; i += 32) {
     cxf<W, C> v;
     xld<W, C>(y, n, i, v);
@@ -959,8 +1052,9 @@ __device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, uint64_t* za, ui
           dot_exp<false, W, C>(zr, zi, rr, ri, er, ei);
         }
         xfn::xfacc<W> ar, ai;
-        xfn::xfacc_init(ar, warp_max(er));
-        if constexpr (C == 2) xfn::xfacc_init(ai, warp_max(ei));
+        const int head = acc_extra_head(C * (c - i));
+        xfn::xfacc_init(ar, warp_max(er) + head);
+        if constexpr (C == 2) xfn::xfacc_init(ai, warp_max(ei) + head);
         for (int k = i + lane; k < c; k += 32) {
           cxf<W, C> zk, rk;
           xld<W, C>(z, n, k, zk);
@@ -1002,6 +1096,223 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrParams p) {
     const int g = (b - p.nAc - p.nAi) * (QR_THREADS / 32) + warp;
     if (g > (n - 1) / 2) return;
     qr_rinv_rows<K, C>(p, g, n - 1 - g, sm + 2 * warp * col, sm + (2 * warp + 1) * col, ep);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same factorization for large n (beyond what the dataflow kernel keeps
+// in shared memory with all its blocks resident): column by column, the
+// working columns in global memory, three plain launches per reflector step
+// and no flag waits.
+//   qrg_init:  Aw = A0 and Yw = I as extended floats (column-major);
+//   qrg_pivot(j):  one warp: the pivot scalars of reflector j from column j
+//     of Aw (rows j..n-1), the quantities of the dataflow kernel: s_j|x_j|,
+//     v_jj, tau_j and 1/R_jj;
+//   qrg_apply(j):  a warp per column c > j of Aw and per column of Yw:
+//     w = x_j^H y + conj(s_j|x_j|) y_j, then y -= tau_j w v_j (rows j..n-1),
+//     which leaves R_jc in row j of column c;
+//   qrg_bsub:  a warp per column e of Yw = Q^H: W e_e = R^{-1} Q^H e_e by
+//     back substitution, w_i = y_i / R_ii and y_k -= R_ki w_i for k < i,
+//     i = n-1..0 (the R entries above the diagonal are in Aw).
+// ---------------------------------------------------------------------------
+template <int K, int C>
+__global__ void qrg_init_kernel(QrParams p) {
+  constexpr int W = xfn::xf_words_t<K>::value;
+  const int n = p.n;
+  const long long nn = (long long)n * n;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nn;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(q / n), i = (int)(q - (long long)c * n);  // q = c*n + i
+    cxf<W, C> v;
+    cxf_load<K, W, C>(p.A0, p.NA, (long long)i * n + c, v);
+    xst<W, C>(p.Aw, nn, q, v);
+    cxf_zero(v);
+    if (i == c) xfn::xf_from_double(1.0, v.re);
+    xst<W, C>(p.Yw, nn, q, v);
+  }
+}
+
+template <int K, int C>
+__global__ void qrg_pivot_kernel(QrParams p, int j) {
+  using namespace xfn;
+  constexpr int W = xf_words_t<K>::value;
+  const int lane = threadIdx.x & 31;
+  const int n = p.n;
+  const long long nn = (long long)n * n;
+  const long long col = (long long)j * n;
+  // N = |x_j|^2 over rows j..n-1 (one fixed-point sum)
+  int er = 2 * XF_ZERO_E, ei = er;
+  for (int i = j + lane; i < n; i += 32) {
+    int yr, yi;
+    xld_exp<W, C>(p.Aw, nn, col + i, yr, yi);
+    dot_exp<true, W, C>(yr, yi, yr, yi, er, ei);
+  }
+  xfacc<W> acc;
+  xfacc_init(acc, warp_max(er) + acc_extra_head(C * (n - j)));
+  for (int i = j + lane; i < n; i += 32) {
+    cxf<W, C> v;
+    xld<W, C>(p.Aw, nn, col + i, v);
+    xfacc_fma(acc, v.re, v.re);
+    if constexpr (C == 2) xfacc_fma(acc, v.im, v.im);
+  }
+  xfacc_warp_sum(acc);
+  xf<W> xN;
+  xfacc_get(acc, xN);
+  const bool singular = xf_is_zero(xN);
+  if (singular) xf_from_double(1.0, xN);  // keep the arithmetic finite; reported below
+  // |x| = N / sqrt(N), s = x_jj / |x_jj| (1 if x_jj = 0), v_jj = x_jj + s|x|,
+  // tau = 1 / (N + |x| |x_jj|), 1 / R_jj = -conj(s) / |x|
+  xf<W> xry, xal, xax0;
+  xf_rsqrt(xN, xry);
+  xf_mul(xN, xry, xal);
+  cxf<W, C> x0;
+  xld<W, C>(p.Aw, nn, col + j, x0);
+  xf<W> sre, sim, sgr, sgi;
+  bool neg = false;
+  if constexpr (C == 1) {
+    neg = x0.re.s != 0;
+    xax0 = x0.re;
+    xax0.s = 0;
+    sre = xal;
+    if (neg) xf_neg(sre);
+    xf_zero(sim);
+  } else {
+    xf<W> t1, t2, a2x, rx;
+    xf_mul(x0.re, x0.re, t1);
+    xf_mul(x0.im, x0.im, t2);
+    xf_add(t1, t2, a2x);
+    const bool z = xf_is_zero(a2x);
+    if (z) xf_from_double(1.0, a2x);
+    xf_rsqrt(a2x, rx);
+    xf_mul(a2x, rx, xax0);
+    xf_mul(x0.re, rx, sgr);
+    xf_mul(x0.im, rx, sgi);
+    if (z) {
+      xf_zero(xax0);
+      xf_from_double(1.0, sgr);
+      xf_zero(sgi);
+    }
+    xf_mul(sgr, xal, sre);
+    xf_mul(sgi, xal, sim);
+  }
+  cxf<W, C> sa, v0, rinv;
+  sa.re = sre;
+  sa.im = sim;
+  xf_add(x0.re, sre, v0.re);
+  xf_add(x0.im, sim, v0.im);
+  cxf<W, 1> tau;
+  xf_zero(tau.im);
+  {
+    xf<W> t1, t2;
+    xf_mul(xal, xax0, t1);
+    xf_add(xN, t1, t2);
+    xf_recip(t2, tau.re);
+  }
+  if constexpr (C == 1) {
+    rinv.re = xry;
+    if (!neg) xf_neg(rinv.re);
+    xf_zero(rinv.im);
+  } else {
+    xf_mul(sgr, xry, rinv.re);
+    xf_neg(rinv.re);
+    xf_mul(sgi, xry, rinv.im);
+  }
+  if (singular) {
+    xf_zero(tau.re);
+    cxf_zero(rinv);
+  }
+  if (lane == 0) {
+    if (singular) atomicOr(p.status, MDN_DEV_SINGULAR);
+    xst<W, C>(p.salpha, p.n, j, sa);
+    xst<W, C>(p.v0, p.n, j, v0);
+    xst<W, 1>(p.tau, p.n, j, tau);
+    xst<W, C>(p.rinv, p.n, j, rinv);
+  }
+}
+
+template <int K, int C>
+__global__ void qrg_apply_kernel(QrParams p, int j) {
+  using namespace xfn;
+  constexpr int W = xf_words_t<K>::value;
+  const int lane = threadIdx.x & 31;
+  const int n = p.n;
+  const long long nn = (long long)n * n;
+  const long long xcol = (long long)j * n;
+  const int na = n - 1 - j;  // columns j+1..n-1 of Aw, then the n columns of Yw
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  cxf<W, 1> tau;
+  xld<W, 1>(p.tau, p.n, j, tau);
+  cxf<W, C> sa, v0;
+  xld<W, C>(p.salpha, p.n, j, sa);
+  xld<W, C>(p.v0, p.n, j, v0);
+  const int head = acc_extra_head(C * (n - j));
+  for (long long t = w0; t < na + n; t += nw) {
+    uint64_t* Y = t < na ? p.Aw : p.Yw;
+    const long long ycol = (t < na ? (long long)(j + 1 + t) : (long long)(t - na)) * n;
+    // dot = x_j^H y over rows j..n-1
+    int er = 2 * XF_ZERO_E, ei = er;
+    for (int i = j + lane; i < n; i += 32) {
+      int xr, xi, yr, yi;
+      xld_exp<W, C>(p.Aw, nn, xcol + i, xr, xi);
+      xld_exp<W, C>(Y, nn, ycol + i, yr, yi);
+      dot_exp<true, W, C>(xr, xi, yr, yi, er, ei);
+    }
+    xfacc<W> ar, ai;
+    xfacc_init(ar, warp_max(er) + head);
+    if constexpr (C == 2) xfacc_init(ai, warp_max(ei) + head);
+    for (int i = j + lane; i < n; i += 32) {
+      cxf<W, C> x, y;
+      xld<W, C>(p.Aw, nn, xcol + i, x);
+      xld<W, C>(Y, nn, ycol + i, y);
+      dot_fma<true>(ar, ai, x, y);
+    }
+    cxf<W, C> w, yj, ng;
+    dot_finish(ar, ai, w);
+    xld<W, C>(Y, nn, ycol + j, yj);
+    cxf_fma<true>(w, sa, yj);  // w = x^H y + conj(s|x|) y_j = v^H y
+    cxf_scale(w, tau.re, ng);
+    cxf_neg(ng);
+    __syncwarp();
+    for (int i = j + lane; i < n; i += 32) {
+      cxf<W, C> v, y;
+      if (i == j) v = v0;
+      else xld<W, C>(p.Aw, nn, xcol + i, v);
+      xld<W, C>(Y, nn, ycol + i, y);
+      cxf_fma<false>(y, ng, v);
+      xst<W, C>(Y, nn, ycol + i, y);
+    }
+    __syncwarp();
+  }
+}
+
+template <int K, int C>
+__global__ void qrg_bsub_kernel(QrParams p) {
+  using namespace xfn;
+  constexpr int W = xf_words_t<K>::value;
+  const int lane = threadIdx.x & 31;
+  const int n = p.n;
+  const long long nn = (long long)n * n;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long e = w0; e < n; e += nw) {
+    const long long ycol = e * n;
+    for (int i = n - 1; i >= 0; --i) {
+      cxf<W, C> yi, ri, wi;
+      xld<W, C>(p.Yw, nn, ycol + i, yi);
+      xld<W, C>(p.rinv, p.n, i, ri);
+      cxf_mul<false>(yi, ri, wi);
+      if (lane == 0) cxf_store<K, W, C>(p.W, p.Nnn, (long long)i * n + e, wi);
+      cxf_neg(wi);
+      for (int k = lane; k < i; k += 32) {
+        cxf<W, C> r, y;
+        xld<W, C>(p.Aw, nn, (long long)i * n + k, r);  // R_ki: row k of column i
+        xld<W, C>(p.Yw, nn, ycol + k, y);
+        cxf_fma<false>(y, r, wi);
+        xst<W, C>(p.Yw, nn, ycol + k, y);
+      }
+      __syncwarp();
+    }
   }
 }
 
@@ -1095,8 +1406,9 @@ __device__ __forceinline__ void warp_rowdot(const double* Mp, long long NM, long
       dot_exp<false, W, C>(ar, ai, xr, xi, er, ei);
     }
     xfn::xfacc<W> acr, aci;
-    xfn::xfacc_init(acr, warp_max(er) + 1);
-    if constexpr (C == 2) xfn::xfacc_init(aci, warp_max(ei) + 1);
+    const int head = acc_extra_head(C * n);
+    xfn::xfacc_init(acr, warp_max(er) + 1 + head);
+    if constexpr (C == 2) xfn::xfacc_init(aci, warp_max(ei) + 1 + head);
     for (int l = lane; l < n; l += 32) {
       cxf<W, C> a, x;
       cxf_load<K, W, C>(Mp, NM, row_off + (long long)l * ms, a);
@@ -1404,6 +1716,105 @@ __global__ void fabry_kernel(LossParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// Residual of the block lower triangular Toeplitz system (Eq. (eqToeplitz);
+// the residual kernels of Sections 5.4 and 6): entry (i, k) is
+//   r_k[i] = b_k[i] - sum_{j=0..k} sum_l A_j[i][l] dx_{k-j}[l],
+// one warp per entry.  For K >= 2 the (k+1) n products and b_k[i] are summed
+// in one fixed-point accumulator per part at a scale from a warp maximum of
+// the leading limbs' exponents (xf.cuh), with headroom for the term count,
+// and rounded to K limbs once.
+// ---------------------------------------------------------------------------
+template <int K, int C>
+__global__ void residual_kernel(ResParams p) {
+  const int lane = threadIdx.x & 31;
+  const int n = p.n, D = p.D;
+  const long long nn = (long long)n * n;
+  const long long items = (long long)n * D;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long q = w0; q < items; q += nw) {
+    const int k = (int)(q / n), i = (int)(q - (long long)k * n);
+    const long long terms = (long long)(k + 1) * n;
+    cmd<K, C> b, res;
+    ld(p.b, p.Nx, (long long)i * D + k, b);
+    if constexpr (K >= 2) {
+      constexpr int W = xfn::xf_words_t<K>::value;
+      int er = lead_exp(b.re[0]);
+      int ei = C == 2 ? lead_exp(b.im[0]) : 2 * xfn::XF_ZERO_E;
+      for (long long t = lane; t < terms; t += 32) {
+        const int j = (int)(t / n), l = (int)(t - (long long)j * n);
+        const long long ia = (long long)j * nn + (long long)i * n + l, ix = (long long)l * D + (k - j);
+        const int ar = lead_exp(p.A[ia]), xr = lead_exp(p.dx[ix]);
+        const int ai = C == 2 ? lead_exp(p.A[p.NA + ia]) : 2 * xfn::XF_ZERO_E;
+        const int xi = C == 2 ? lead_exp(p.dx[p.Nx + ix]) : 2 * xfn::XF_ZERO_E;
+        dot_exp<false, W, C>(ar, ai, xr, xi, er, ei);
+      }
+      const int head = acc_extra_head(C * terms + 1);
+      xfn::xfacc<W> acr, aci;
+      xfn::xfacc_init(acr, warp_max(er) + 1 + head);
+      if constexpr (C == 2) xfn::xfacc_init(aci, warp_max(ei) + 1 + head);
+      // acc = sum A dx - b (b once, from lane 0); the residual is -acc
+      if (lane == 0) {
+        xfn::xf<W> one, bx;
+        xfn::xf_from_double(1.0, one);
+        xfn::xf_from_md<K, W>(b.re, bx);
+        xfn::xfacc_fma(acr, bx, one, true);
+        if constexpr (C == 2) {
+          xfn::xf_from_md<K, W>(b.im, bx);
+          xfn::xfacc_fma(aci, bx, one, true);
+        }
+      }
+      for (long long t = lane; t < terms; t += 32) {
+        const int j = (int)(t / n), l = (int)(t - (long long)j * n);
+        cxf<W, C> a, x;
+        cxf_load<K, W, C>(p.A, p.NA, (long long)j * nn + (long long)i * n + l, a);
+        cxf_load<K, W, C>(p.dx, p.Nx, (long long)l * D + (k - j), x);
+        dot_fma<false>(acr, aci, a, x);
+      }
+      cxf<W, C> sum;
+      dot_finish(acr, aci, sum);
+      cxf_neg(sum);
+      xfn::xf_to_md<K, W>(sum.re, res.re);
+      if constexpr (C == 2) xfn::xf_to_md<K, W>(sum.im, res.im);
+      else md_zero(res.im);
+    } else {
+      CAcc<K, C> acc;
+      cacc_zero(acc);
+      for (long long t = lane; t < terms; t += 32) {
+        const int j = (int)(t / n), l = (int)(t - (long long)j * n);
+        cmd<K, C> a, x;
+        ld(p.A, p.NA, (long long)j * nn + (long long)i * n + l, a);
+        ld(p.dx, p.Nx, (long long)l * D + (k - j), x);
+        cacc_fma(acc, a, x);
+      }
+      cmd<K, C> s;
+      warp_sum_acc(acc, s);
+      cmd_sub(b, s, res);
+    }
+    if (lane == 0) {
+      if (p.r) st(p.r, p.Nx, (long long)i * D + k, res);
+      const bool in = !p.resmask || p.resmask[i];
+      p.resabs[(long long)i * D + k] = !in ? 0.0 : (C == 2) ? hypot(res.re[0], res.im[0]) : fabs(res.re[0]);
+    }
+  }
+}
+
+// out = s a for every entry of an md array (md multiplication, the complex
+// one for C = 2); s is one md value.
+template <int K, int C>
+__global__ void scale_kernel(ScaleParams p) {
+  cmd<K, C> s;
+  ld(p.s, 1, 0, s);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < p.N;
+       q += (long long)gridDim.x * blockDim.x) {
+    cmd<K, C> a, r;
+    ld(p.a, p.N, q, a);
+    cmd_mul(s, a, r);
+    st(p.out, p.N, q, r);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers of one (K, C) instantiation
 // ---------------------------------------------------------------------------
 inline int grid_for(long long work, int threads) {
@@ -1438,7 +1849,8 @@ cudaError_t launch_ed(const EdParams& p, int grid, cudaStream_t s) {
 }
 template <int K, int C>
 cudaError_t launch_a0(const A0Params& p, cudaStream_t s) {
-  a0_partials_kernel<K, C><<<(p.nnz + 127) / 128, 128, 0, s>>>(p);
+  if (p.kmax > 32) a0_partials_warp_kernel<K, C><<<grid_for((long long)p.M * 32, 128), 128, 0, s>>>(p);
+  else a0_partials_kernel<K, C><<<(p.nnz + 127) / 128, 128, 0, s>>>(p);
   a0_assemble_kernel<K, C><<<grid_for((long long)p.n * p.n, 128), 128, 0, s>>>(p);
   return cudaGetLastError();
 }
@@ -1459,7 +1871,21 @@ cudaError_t launch_assemble(const AsmParams& p, bool want_A, cudaStream_t s) {
 // two blocks share an SM: each column warp then has its sub-partition's FP64
 // pipe to itself, which sets the length of the sequential column chain.
 template <int K, int C>
+cudaError_t launch_qr_large(const QrParams& p, cudaStream_t s) {
+  const int n = p.n;
+  qrg_init_kernel<K, C><<<grid_for((long long)n * n, 256), 256, 0, s>>>(p);
+  for (int j = 0; j < n; ++j) {
+    qrg_pivot_kernel<K, C><<<1, 32, 0, s>>>(p, j);
+    const long long cols = (long long)(n - 1 - j) + n;  // a warp per column
+    qrg_apply_kernel<K, C><<<grid_for(cols * 32, 128), 128, 0, s>>>(p, j);
+  }
+  qrg_bsub_kernel<K, C><<<(n + 3) / 4, 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int K, int C>
 cudaError_t launch_qr(const QrParams& p, cudaStream_t s) {
+  if (p.large) return launch_qr_large<K, C>(p, s);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(qr_kernel<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_MAX);
@@ -1496,6 +1922,16 @@ cudaError_t launch_fsub(const FsubParams& p, cudaStream_t s) {
 template <int K, int C>
 cudaError_t launch_stage0(const FsubParams& p, cudaStream_t s) {
   stage0_kernel<K, C><<<(p.n + 3) / 4, 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+template <int K, int C>
+cudaError_t launch_residual(const ResParams& p, cudaStream_t s) {
+  residual_kernel<K, C><<<grid_for((long long)p.n * p.D * 32, 128), 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+template <int K, int C>
+cudaError_t launch_scale(const ScaleParams& p, cudaStream_t s) {
+  scale_kernel<K, C><<<grid_for(p.N, 128), 128, 0, s>>>(p);
   return cudaGetLastError();
 }
 template <int K, int C>

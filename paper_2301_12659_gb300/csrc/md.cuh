@@ -32,7 +32,9 @@
 // Error bounds (sloppy semantics, as for the QD library's default add): for
 // K limbs, |md_add(a,b) - (a+b)| <= c_K 2^(-53K) (|a| + |b|) and
 // |md_mul(a,b) - ab| <= c_K 2^(-53K) |ab| with c_K a small constant (<= 2K^2);
-// checked against exact rationals by the GPU tests.
+// the reciprocal, the quotient and the square roots to c_K 2^(-53K) relative;
+// checked against exact rationals on the GPU through a test-only probe
+// kernel (tests/native/md_probe.cu).
 #pragma once
 #include <cstdint>
 
@@ -399,7 +401,26 @@ __device__ __forceinline__ void md_div(const double (&a)[K], const double (&b)[K
   md_mul(a, y, r);
 }
 
+// One Newton correction y += y (1 - a y^2) / 2 with every product at K limbs.
+template <int K>
+__device__ __forceinline__ void md_rsqrt_refine(const double (&a)[K], double (&y)[K]) {
+  double q[K], p[K], one[K], e[K], c[K];
+  md_mul(a, y, q);
+  md_mul(q, y, p);
+  md_zero(one);
+  one[0] = 1.0;
+  md_sub(one, p, e);
+#pragma unroll
+  for (int l = 0; l < K; ++l) e[l] *= 0.5;  // exact
+  md_mul(y, e, c);
+  md_add(y, c, y);
+}
+
 // y = 1 / sqrt(a), a > 0: the same scheme with y = y_h + y_h (1 - a y_h^2) / 2.
+// The seed 1/sqrt in double carries two roundings, and each level squares the
+// error of the level below (times 3/2), so the half-width value gets one more
+// correction at its own width before the step to K limbs (K >= 4): without
+// it the octo double result would keep only about 406 of its 424 bits.
 template <int K>
 __device__ __forceinline__ void md_rsqrt(const double (&a)[K], double (&y)[K]) {
   if constexpr (K == 1) {
@@ -410,6 +431,7 @@ __device__ __forceinline__ void md_rsqrt(const double (&a)[K], double (&y)[K]) {
 #pragma unroll
     for (int l = 0; l < H; ++l) ah[l] = a[l];
     md_rsqrt<H>(ah, yh);
+    if constexpr (H >= 2) md_rsqrt_refine<H>(ah, yh);
     double q[K], p[K], one[K], e[K];
     md_mul_part<K, H>(a, yh, q);
     md_mul_part<K, H>(q, yh, p);

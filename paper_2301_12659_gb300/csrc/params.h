@@ -66,6 +66,7 @@ struct A0Params {
   const int* pair_slot;
   double* A;            // A_0 written into the j = 0 slice of [K][C][D][n][n]
   long long NA;
+  int kmax;             // largest monomial: beyond 32 variables a warp per monomial
 };
 
 struct AsmParams {
@@ -105,6 +106,12 @@ struct QrParams {
   const unsigned* epoch;
   int* status;
   long long spin_limit;  // nanoseconds a flag wait may last
+  // column-by-column variant for large n (no waits): the columns of A0 and
+  // of the identity under the reflectors, as extended floats, column-major
+  // ([W+1][C][n columns][n rows], element (i, c) at c*n + i)
+  int large;
+  uint64_t* Aw;
+  uint64_t* Yw;
 };
 
 // Persistent forward substitution (one cooperative launch per solve).
@@ -183,6 +190,27 @@ struct LossParams {
   double* g;     // [K][1][n][D]
 };
 
+// Residual of the block Toeplitz system (mdn_residual): one warp per entry.
+struct ResParams {
+  int n, D;
+  const double* A;
+  long long NA;  // D*n*n
+  const double* b;
+  const double* dx;
+  long long Nx;  // n*D
+  double* r;         // md residual series [K][C][n][D] (may be null)
+  double* resabs;    // |leading double| per entry, zero outside the row sample
+  const int* resmask;  // rows in the sampled norm (null: all)
+};
+
+// out = s * a for one md scalar s and an md array a (mdn_md_scale).
+struct ScaleParams {
+  const double* s;  // [K][C] (N = 1)
+  const double* a;
+  double* out;
+  long long N;
+};
+
 // ---- batched systems (one persistent launch) ----
 struct BatchSys {
   int n, D, M, mono0;      // monomials mono0 .. mono0+M-1 (global numbering)
@@ -257,6 +285,8 @@ struct KernelTable {
   cudaError_t (*fabry)(const LossParams&, cudaStream_t);
   cudaError_t (*batch)(const BatchParams&, int blocks, int threads, cudaStream_t);
   int (*batch_occupancy)(int threads);  // resident blocks per SM
+  cudaError_t (*residual)(const ResParams&, cudaStream_t);
+  cudaError_t (*scale)(const ScaleParams&, cudaStream_t);
 };
 
 const KernelTable* kernels_for(int K, int C);

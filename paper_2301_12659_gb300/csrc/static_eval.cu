@@ -64,6 +64,12 @@ __global__ void static_eval_kernel(StaticParams p) {
     ld(p.cst, Nx, (long long)i * D + k2, v);
     cacc_set(acc2, v);
   }
+  // warp 0 checks every equation index (a monomial of no equation 0..n-1
+  // would otherwise be skipped silently)
+  if (i == 0) {
+    for (int m = lane; m < p.M; m += 32)
+      if (p.eq[m] < 0 || p.eq[m] >= p.n) atomicOr(status, 1);
+  }
   for (int m = 0; m < p.M; ++m) {
     if (p.eq[m] != i) continue;
     const int vp = p.vptr[m], k = p.vptr[m + 1] - vp;

@@ -32,7 +32,8 @@ EXPORTS = ("mdn_create", "mdn_workspace_bytes", "mdn_load_system", "mdn_set_seri
            "mdn_get_series", "mdn_get_residual", "mdn_evaluate", "mdn_solve", "mdn_profile",
            "mdn_status_word", "mdn_last_error", "mdn_destroy", "mdn_evaluate_static", "mdn_set_late_updates", "mdn_adjoint", "mdn_fabry_loss", "mdn_set_residual_rows", "mdn_set_stagger",
            "mdn_ed_schedule", "mdn_batch_create", "mdn_batch_workspace_bytes", "mdn_batch_load", "mdn_batch_evaluate",
-           "mdn_batch_solve", "mdn_batch_tiles", "mdn_batch_last_error", "mdn_batch_destroy")
+           "mdn_batch_solve", "mdn_batch_tiles", "mdn_batch_last_error", "mdn_batch_destroy", "mdn_residual",
+           "mdn_md_scale", "mdn_set_wait_limit_ns")
 BATCH_CONVERGED, BATCH_SINGULAR, BATCH_NONFINITE = 1, 2, 4
 MDN_NUM_PHASES = 5
 PHASES = ("evaluate", "assemble", "qr", "forward", "update")
@@ -73,6 +74,9 @@ def load(path: str = None) -> ctypes.CDLL:
     L.mdn_set_residual_rows.argtypes = [P, P, I]
     L.mdn_set_stagger.argtypes = [P, I]
     L.mdn_fabry_loss.argtypes = [P, P, P, P]
+    L.mdn_residual.argtypes = [P, P, P, P, P, ctypes.POINTER(D)]
+    L.mdn_md_scale.argtypes = [P, P, P, ctypes.c_int64, P]
+    L.mdn_set_wait_limit_ns.argtypes = [P, ctypes.c_int64]
     L.mdn_batch_create.argtypes = [ctypes.POINTER(P), I, I, I, P, P, P, I, I]
     L.mdn_batch_workspace_bytes.argtypes = [P, P]
     L.mdn_batch_workspace_bytes.restype = ctypes.c_size_t
@@ -228,6 +232,22 @@ def mdn_set_residual_rows(ctx, rows) -> int:
     return load().mdn_set_residual_rows(ctx, p if a.size else None, int(a.size))
 
 
+def mdn_residual(ctx, A, b, dx, r_out=None):
+    """Returns (status, norm): the residual b_k - sum_{j<=k} A_j dx_{k-j}
+    into r_out (device, may be None) and its 1-norm of leading doubles."""
+    norm = ctypes.c_double(0.0)
+    st = load().mdn_residual(ctx, _ptr(A), _ptr(b), _ptr(dx), _ptr(r_out), ctypes.byref(norm))
+    return st, norm.value
+
+
+def mdn_md_scale(ctx, s, a, count: int, out) -> int:
+    return load().mdn_md_scale(ctx, _ptr(s), _ptr(a), int(count), _ptr(out))
+
+
+def mdn_set_wait_limit_ns(ctx, limit_ns: int) -> int:
+    return load().mdn_set_wait_limit_ns(ctx, int(limit_ns))
+
+
 def mdn_set_stagger(ctx, first_steps: int) -> int:
     return load().mdn_set_stagger(ctx, int(first_steps))
 
@@ -284,6 +304,7 @@ class Newton:
 
     def newton(self, steps: int, tol: float = 0.0):
         st, done, hist = mdn_newton(self.ctx, steps, tol)
+        self.steps_done = done
         if st not in (MDN_OK,):
             raise MdnError(st, mdn_last_error(self.ctx))
         return hist
@@ -322,6 +343,29 @@ class Newton:
         g = self.torch.empty_like(x)
         _check(self.ctx, mdn_fabry_loss(self.ctx, x.contiguous(), loss, g))
         return loss, g
+
+    def residual(self, A, b, dx, want_r: bool = True):
+        """(r or None, ||r||_1) of r_k = b_k - sum_{j<=k} A_j dx_{k-j}."""
+        dev = self.cst.device
+        A, b, dx = (t if isinstance(t, self.torch.Tensor) else self.torch.as_tensor(np.ascontiguousarray(t), device=dev)
+                    for t in (A, b, dx))
+        r = self.torch.empty(self.shape_series, dtype=self.torch.float64, device=dev) if want_r else None
+        st, norm = mdn_residual(self.ctx, A.contiguous(), b.contiguous(), dx.contiguous(), r)
+        _check(self.ctx, st)
+        return r, norm
+
+    def md_scale(self, s, a):
+        """s * a entry by entry (md multiplication) for one md value s
+        ([K, C]) and an md array a ([K, C, ...])."""
+        a = a.contiguous()
+        out = self.torch.empty_like(a)
+        count = a[0, 0].numel()
+        _check(self.ctx, mdn_md_scale(self.ctx, s.contiguous(), a, count, out))
+        return out
+
+    def set_wait_limit_ns(self, limit_ns: int):
+        """Bound of every device wait (nanoseconds; default 2e9)."""
+        _check(self.ctx, mdn_set_wait_limit_ns(self.ctx, limit_ns))
 
     def set_residual_rows(self, rows):
         """Residual monitor on these rows only (scaled by n/len(rows)); an

@@ -380,3 +380,52 @@ def one_column_system(n: int, d: int, K: int, C: int = 1, index: int = 5, delta:
     sysm = System(K, C, n, d, eq, vptr, vidx, coeff, np.zeros((K, C, n, D)), f"one-column-n{n}-d{d}-K{K}")
     sysm.check()
     return sysm, x
+
+
+def section3_system(n: int, d: int, K: int, columns: int = 1, index: int = 6, delta: float = 0.1,
+                    noise: float = 1e-3):
+    """The columns-of-monomials systems of Section 3 for Newton: one column,
+    x_0 x_1 ... x_i = b_i(t), or two columns, c1_i x_0...x_i +
+    c2_i x_0...x_{n-1-i} = b_i(t) (the second exponent matrix has the rows of
+    the first in reverse order), with the solution x_v(t) = exp(alpha_v t),
+    alpha_v uniform in [-1, -1+delta] u [1-delta, 1].  The right hand sides
+    b_i are the exponential series of the partial sums of the alpha_v (times
+    c1_i, c2_i), held in the leading limb (double precision inputs).
+    Returns (System with the constant term -b, start series: 1 + noise in
+    the leading limb of x_0, every higher coefficient 0)."""
+    D = d + 1
+    seed = BASE_SEED + index
+    u = 0.5 * (uniform_pm1(substream_seed(seed, 1), 4 * n) + 1.0)
+    alpha = (1.0 - delta * u[:n]) * np.where(u[n:2 * n] < 0.5, -1.0, 1.0)
+    eq, vlists, cvals = [], [], []
+    c1 = 0.5 + u[2 * n:3 * n] if columns == 2 else np.ones(n)
+    c2 = u[3 * n:] - 1.5
+    for i in range(n):
+        eq.append(i)
+        vlists.append(np.arange(i + 1))
+        cvals.append(c1[i])
+        if columns == 2:
+            eq.append(i)
+            vlists.append(np.arange(n - i))
+            cvals.append(c2[i])
+    M = len(eq)
+    vptr = np.concatenate([[0], np.cumsum([len(v) for v in vlists])]).astype(np.int32)
+    vidx = np.concatenate(vlists).astype(np.int32)
+    coeff = np.zeros((K, 1, M, D))
+    coeff[0, 0, :, 0] = cvals
+    fact = np.array([float(math.factorial(j)) for j in range(D)])
+    csum = np.cumsum(alpha)
+    cst = np.zeros((K, 1, n, D))
+    for i in range(n):
+        s1 = csum[i]
+        b = c1[i] * s1 ** np.arange(D) / fact
+        if columns == 2:
+            s2 = csum[n - 1 - i]
+            b = b + c2[i] * s2 ** np.arange(D) / fact
+        cst[0, 0, i] = -b
+    x0 = np.zeros((K, 1, n, D))
+    x0[0, 0, :, 0] = 1.0 + noise * uniform_pm1(substream_seed(seed, 2), n)
+    sysm = System(K, 1, n, d, np.asarray(eq, np.int32), vptr, vidx, coeff, cst,
+                  f"section3-{columns}col-n{n}-d{d}-K{K}", meta={"alpha": alpha})
+    sysm.check()
+    return sysm, x0

@@ -67,6 +67,42 @@ def test_autograd_functions(md):
     assert abs(float(L[0].detach()) - L_ref[0]) <= 1e-15 * abs(L_ref[0])
 
 
+def test_autograd_upstream_gradient_is_applied_in_md(md):
+    """A seed that is not a power of two ((L[0] / 3).backward(): the
+    incoming gradient is the double 1/3) scales dL/dc in md on the device:
+    the gradient is the oracle's adjoint of the exact scaled g, to 1e-24.
+    Two forwards before the backwards: each graph keeps the coefficients of
+    its own forward."""
+    import torch
+    from paper_2301_12659_gb300.autograd import FabryLoss, NewtonSeries
+    cfg = wl.small_config(2, 1, n=6, d=11, mono_per_eq=3, kmin=1, kmax=4, steps=8, index=534)
+    s, xstar, x0 = planted(cfg)
+    nw = md.Newton(s)
+    x0d = torch.as_tensor(x0, device=nw.coeff.device)
+    c1 = nw.coeff.clone().requires_grad_(True)
+    x1 = NewtonSeries.apply(c1, nw, x0d, cfg.steps)
+    L1 = FabryLoss.apply(x1, nw)
+    # a second forward on the same context with other coefficients
+    c2_np = s.coeff.copy()
+    c2_np[:, :, 0, 3] *= 0.5
+    c2 = torch.as_tensor(c2_np, device=nw.coeff.device).requires_grad_(True)
+    x2 = NewtonSeries.apply(c2, nw, x0d, cfg.steps)
+    L2 = FabryLoss.apply(x2, nw)
+    (L1[0] / 3.0).backward()
+    L2[0].backward()
+    third = Fr(1, 3)
+    seed = float(third)  # the double the division hands down
+    for c, x, coeff_np in ((c1, x1, s.coeff), (c2, x2, c2_np)):
+        sc = wl.System(s.K, s.C, s.n, s.d, s.eq, s.vptr, s.vidx, coeff_np, s.cst)
+        _, g_ref = oracle.fabry_loss(to_np(x.detach()))
+        grad_ref = oracle.adjoint(sc, to_np(x.detach()), g_ref)
+        if c is c1:
+            grad_ref = oracle.md_binary("mul", grad_ref.reshape(s.K, 1, -1),
+                                        np.broadcast_to(np.array([seed] + [0.0] * (s.K - 1)).reshape(s.K, 1, 1),
+                                                        (s.K, 1, grad_ref[0, 0].size))).reshape(grad_ref.shape)
+        assert _close(to_np(c.grad), grad_ref) <= REL
+
+
 def _promote(a, K=8):
     out = np.zeros((K,) + a.shape[1:])
     out[:a.shape[0]] = a

@@ -142,7 +142,7 @@ def test_nonfinite_series_is_reported(md):
     nw.set_series(x0)
     with pytest.raises(md.MdnError) as e:
         nw.newton(1)
-    assert e.value.status in (md.MDN_ENONFINITE, md.MDN_ESINGULAR)
+    assert e.value.status == md.MDN_ENONFINITE
 
 
 NEWTON_CASES = [
@@ -164,10 +164,26 @@ def test_newton_matches_oracle_and_plant(md, cfg):
     x = to_np(nw.series())
     assert np.max(mt.series_rel_error(x, x_ref)) <= cfg.tol
     assert np.max(mt.series_rel_error(x, xstar)) <= cfg.tol
-    # ||f|| before each update agrees where it is above the rounding level
-    big = h_ref[:, 0] > 1e-6
-    assert np.allclose(hist[big, 0], h_ref[big, 0], rtol=1e-10)
-    assert hist[-1, 0] < 1e3 * cfg.tol and hist[-1, 1] < 1e3 * cfg.tol
+    _check_history(hist, h_ref, cfg.K, s.n * s.D, cfg.tol)
+
+
+def _check_history(hist, h_ref, K, entries, tol):
+    """The three history columns against the oracle's (Section 2 pseudo
+    code): ||f||_1 and ||dx||_1 where they are above the rounding level of
+    the series (there the two sides agree to far more than 1e-10), the
+    monitor ||b - A dx||_1 at the md rounding level of the step on both
+    sides (the residual of a computed solve is rounding noise, so its value
+    is not reproducible across implementations, only its size)."""
+    assert hist.shape == h_ref.shape
+    big0 = h_ref[:, 0] > 1e-6
+    assert np.allclose(hist[big0, 0], h_ref[big0, 0], rtol=1e-10)
+    big2 = h_ref[:, 2] > tol ** 0.5
+    assert big2[0]
+    assert np.allclose(hist[big2, 2], h_ref[big2, 2], rtol=1e-10)
+    eps = 2.0 ** (12 - 52 * K)
+    bound = eps * entries * np.maximum(1.0, h_ref[:, 0])
+    assert np.all(hist[:, 1] <= bound) and np.all(h_ref[:, 1] <= bound)
+    assert hist[-1, 0] < 1e3 * tol
 
 
 @pytest.mark.parametrize("K", [2, 4])
@@ -244,6 +260,51 @@ def test_newton_late_updates_recovers_plant(md):
     assert np.max(mt.series_rel_error(x, x_ref)) <= cfg.tol
 
 
+RESIDUAL_CASES = [(1, 1, 6, 9), (2, 1, 7, 15), (4, 1, 33, 31), (4, 2, 9, 7), (8, 1, 5, 20), (8, 2, 4, 5),
+                  (2, 1, 1, 0)]
+
+
+@pytest.mark.parametrize("K,C,n,d", RESIDUAL_CASES)
+def test_residual_matches_oracle(md, K, C, n, d):
+    """mdn_residual (r_k = b_k - sum_{j<=k} A_j dx_{k-j}, Sections 5.4 and 6)
+    against the oracle's exact-then-round residual, entry by entry, for a dx
+    perturbed off the solution so that r sits far above the rounding level
+    (2^(-26K) of the terms, against a tolerance of 2^(8-53K) of them); its
+    norm and the sampled norm over a subset of rows (scaled by n / rows)."""
+    D = d + 1
+    A = wl.random_md((D, n, n), K, C, 70 + n + K)
+    for i in range(n):
+        A[0, 0, 0, i, i] += n
+    b = wl.random_md((n, D), K, C, 71 + n)
+    dx = oracle.solve(A, b)
+    pert = wl.random_md((n, D), K, C, 72 + n) * 2.0 ** (-26 * K)
+    dx = oracle.md_binary("add", dx.reshape(K, C, -1), pert.reshape(K, C, -1)).reshape(dx.shape)
+    r_ref, norm_ref = oracle.toeplitz_residual(A, b, dx)
+    cfg = wl.small_config(K, C, n=n, d=d, mono_per_eq=1, kmin=1, kmax=1, index=809)
+    s, _, _ = planted(cfg, with_cst=False)
+    nw = _newton(md, s)
+    r, norm = nw.residual(A, b, dx)
+    r = to_np(r)
+    # size of the terms of each entry (leading doubles)
+    Am = mt.magnitude(A[0])  # [D, n, n]
+    xm = mt.magnitude(dx[0])  # [n, D]
+    size = mt.magnitude(b[0]).copy()
+    for k in range(D):
+        for j in range(k + 1):
+            size[:, k] += Am[j] @ xm[:, k - j]
+    err = mt.magnitude(mt.md_diff(r, r_ref))
+    assert np.all(err <= 2.0 ** (8 - 53 * K) * size)
+    assert np.median(mt.magnitude(mt.md_value(r_ref)) / size) >= 2.0 ** (-26 * K - 8)
+    # the norms sum leading doubles: they agree to the entries' error bound
+    slack = 2.0 ** (8 - 53 * K) * size
+    assert abs(norm - norm_ref) <= 1e-12 * norm_ref + slack.sum()
+    rows = [n - 1] if n == 1 else [0, n - 1]
+    nw.set_residual_rows(rows)
+    _, part = nw.residual(A, b, dx, want_r=False)
+    _, part_ref = oracle.toeplitz_residual(A, b, dx, rows=rows)
+    assert abs(part - part_ref) <= 1e-12 * part_ref + n / len(rows) * slack[rows].sum()
+
+
 def test_sampled_residual_monitor(md):
     """The monitor on a subset of rows is that subset's share scaled by
     n / rows: the full monitor splits exactly into a sample and its
@@ -300,12 +361,12 @@ def test_staggered_newton_matches_oracle(md, K, C, n, d, first, steps):
 
 
 def test_evaluation_only_context_beyond_the_qr_limit(md):
-    """n = 300 > MDN_MAX_N: the paper's one-column system (monomial i =
-    x_0...x_i, up to 300 variables) evaluates, rows of f and of the Jacobian
-    match the oracle; the solve calls refuse.  Quad double: a product of 60
-    series of mixed-sign exponentials cancels by ~1e4, which a double double
-    result shows at its last digits (2e-28 against 1e-28)."""
-    K, n, d = 4, 300, 11
+    """n = 1100 > MDN_MAX_N: the paper's one-column system (monomial i =
+    x_0...x_i, up to 1100 variables) evaluates, rows of f and of the
+    Jacobian match the oracle; the solve calls refuse.  Quad double: a
+    product of 60 series of mixed-sign exponentials cancels by ~1e4, which a
+    double double result shows at its last digits (2e-28 against 1e-28)."""
+    K, n, d = 4, 1100, 11
     s, x = wl.one_column_system(n, d, K)
     nw = _newton(md, s)
     f, A = nw.evaluate(x)
@@ -326,9 +387,9 @@ def test_evaluation_only_context_beyond_the_qr_limit(md):
 
 
 def test_newton_at_the_largest_n(md):
-    """n = MDN_MAX_N = 192 (the QR launch at its largest: 120 blocks, one per
-    SM): Newton against the oracle and the plant; one past the evaluation
-    limit is refused at creation."""
+    """n = MDN_MAX_N_DATAFLOW = 192 (the dataflow QR launch at its largest:
+    120 blocks, one per SM): Newton against the oracle and the plant; one
+    past the evaluation limit is refused at creation."""
     cfg = wl.small_config(2, 1, n=192, d=3, mono_per_eq=1, kmin=1, kmax=2, steps=5, index=512)
     s, xstar, x0 = planted(cfg)
     x_ref, _ = oracle.newton(s, x0, cfg.steps)

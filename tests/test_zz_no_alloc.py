@@ -60,3 +60,29 @@ def test_static_evaluation_rejects_sizes_beyond_its_array(md):
     st = md.mdn_evaluate_static(8, 1, 128, 63, 1, 1, idx, idx, idx, dummy, dummy, dummy, dummy,
                                 torch.cuda.current_stream().cuda_stream)
     assert st == md.MDN_ETOOLARGE
+
+
+@pytest.mark.parametrize("bad", ["eq", "var_idx", "var_ptr"])
+def test_static_evaluation_rejects_indices_out_of_range(md, bad):
+    """An equation index, a variable index or a CSR offset out of range is
+    found on the device and reported as MDN_EINVAL (the kernel checks each
+    index before it uses it)."""
+    import torch
+    cfg = wl.small_config(2, 1, n=5, d=7, mono_per_eq=2, kmin=1, kmax=3, index=952)
+    s, xstar, x0 = wl.planted_system(cfg)
+    s.cst = wl.random_md((s.n, s.D), s.K, s.C, 18)
+    eq, vptr, vidx = s.eq.copy(), s.vptr.copy(), s.vidx.copy()
+    if bad == "eq":
+        eq[3] = s.n
+    elif bad == "var_idx":
+        vidx[4] = s.n + 2
+    else:
+        vptr[2] = vptr[-1] + 7
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(a, device=dev)
+    coeff, cst = t(s.coeff), t(s.cst)
+    x = t(wl.random_md((s.n, s.D), s.K, s.C, 41))
+    f = torch.zeros_like(cst)
+    st = md.mdn_evaluate_static(s.K, s.C - 1, s.n, s.d, s.M, int(s.vptr[-1]), t(eq), t(vptr), t(vidx), coeff, cst, x,
+                                f, torch.cuda.current_stream().cuda_stream)
+    assert st == md.MDN_EINVAL

@@ -14,10 +14,12 @@ Output: one JSON line (rank 0).  ``value`` is Newton steps/s over all ranks
 from CUDA events around each timed step (inputs resident in HBM, L2 flushed
 between steps); ``e2e`` times whole solves through the public API with the
 start series copied from pinned host memory and the solution copied back;
-``roofline`` reports the phase with the largest share of device time against
-the integer pipe peak (its md multiply-adds x the integer instructions one
-costs in integer limbs); ``cpu_baseline`` times the CPU oracle on a bounded
-sample.
+``roofline`` reports the phase with the largest share of device time: the
+method's md multiply-adds of that phase per second, against the peak of the
+pipe it runs on (integer instructions, measured at the start of the run by
+peaks/peak_probe.cu), with the FP64-equivalent fraction and the paper's
+Table 2 convention beside it; ``cpu_baseline`` times the CPU oracle on a
+bounded sample (all host threads, and one step on a single thread).
 
 ``--impl reference`` times the CPU oracle (the plain multiple double
 implementation the tests check the GPU against) on the same workload.
@@ -40,24 +42,20 @@ sys.path.insert(0, ROOT)
 from paper_2301_12659_gb300 import flops as F  # noqa: E402
 from paper_2301_12659_gb300 import workloads as wl  # noqa: E402
 
-# FP64 pipe peak of one GB300: 152 SMs x 1.684 FP64 lane operations per clock
-# per SM (measured: one warp instruction per 64 cycles per sub-partition,
-# ~76 with all four busy) x the 2070 MHz maximum SM clock.
-FP64_LANES_PER_CLK_PER_SM = 1.684
-NUM_SMS = 152
-SM_MAX_MHZ = 2070.0
-FP64_PEAK_OPS = NUM_SMS * FP64_LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
-# Integer pipe peak: 152 SMs x 64 integer lane operations per clock per SM
-# (measured: IMAD and LOP3 each) x 2070 MHz.  The evaluation, the QR and the
-# forward substitution compute md values in integer limbs (extended floats
-# and fixed-point accumulators), so their roofline is this pipe.
-INT_LANES_PER_CLK_PER_SM = 64
-INT_PEAK_OPS = NUM_SMS * INT_LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
-# Integer thread instructions per md multiply-add in integer limbs, by
-# limbs (real data): measured with ncu on ed_kernel at the quad double
-# workload, 2.591e9 integer instructions for 12 070 x 528 = 6.37e6
-# multiply-adds (operand conversions and the accumulator included).
+# Roofline denominators: the peaks of the FP64 and integer pipes are measured
+# at the start of every run by the microbenchmarks of
+# paper_2301_12659_gb300/peaks/peak_probe.cu (PEAKS below), and reported in
+# the JSON line.  The evaluation, the QR and the forward substitution
+# compute md values in integer limbs (extended floats and fixed-point
+# accumulators), so their pipe is the integer one: its peak is the measured
+# rate of an even IMAD/LOP3 mix (the instruction kinds of that arithmetic).
+# The method's work is counted in md multiply-adds (flops.method_counts);
+# one real md multiply-add in integer limbs costs this many integer thread
+# instructions (operand conversions and the accumulator included), measured
+# with ncu on ed_kernel (profiles/ed_kernel_int_per_fma.md):
 XF_INT_OPS_PER_FMA = {4: 406.6}
+NUM_SMS = 152
+PEAKS = {}
 
 METRIC = "Newton steps/s (qd, n=64, d=31)"
 
@@ -82,6 +80,13 @@ def parse():
     ap.add_argument("--cpu-threads", type=int, default=0,
                     help="host threads of the CPU oracle (0: all cores; 1 times it single-threaded)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-single-thread", default="on", choices=["on", "off"],
+                    help="also time one oracle step on a single host thread")
+    ap.add_argument("--table4", action="store_true",
+                    help="instead: Newton on the paper's Table 4 workloads (one- and two-column systems, "
+                         "n=1024, 64 coefficients, octo double, 24 staggered steps) with per-phase times")
+    ap.add_argument("--peaks", action="store_true",
+                    help="instead: measure and print the FP64 and integer pipe peaks (peak_probe.cu)")
     ap.add_argument("--batched", default="on", choices=["on", "off"],
                     help="also time the batched workload (4096 quad double systems) and the same systems one by one")
     ap.add_argument("--adjoint", default="on", choices=["on", "off"],
@@ -192,6 +197,22 @@ def oracle_sample(cfg, nsteps, threads=0):
     oracle.newton(s, x0, nsteps)
     dt = time.perf_counter() - t0
     return dt, oracle.get_threads()
+
+
+def oracle_single_thread_step(cfg):
+    """Seconds of one oracle Newton step on one host thread, at the series
+    that 5 steps reached (all host threads for those)."""
+    from oracle import oracle
+    s, xstar, x0 = wl.planted_system(cfg)
+    s.cst = oracle.planted_constant(s, xstar)
+    x5, _ = oracle.newton(s, x0, 5)
+    all_threads = oracle.get_threads()
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.newton(s, x5, 1)
+    dt = time.perf_counter() - t0
+    oracle.set_threads(all_threads)
+    return dt
 
 
 def run_reference(args, cfg):
@@ -317,8 +338,9 @@ def run_batched(args, dev):
                                  "number of updates the batch applied to it, scaled by the class counts"},
         "speedup_vs_one_by_one": one_ms / ms, "generate_s": gen_s,
         "roofline": {"bound": "alu", "kernel": "batch_kernel", "ops_per_launch": ops,
-                     "achieved": ops / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_OPS / 1e12, "unit": "FP64 Tops/s",
-                     "frac": ops / (ms * 1e-3) / FP64_PEAK_OPS},
+                     "achieved": ops / (ms * 1e-3) / 1e12, "peak": PEAKS["fp64_fma"]["ops_per_s"] / 1e12,
+                     "unit": "FP64 Tops/s", "frac": ops / (ms * 1e-3) / PEAKS["fp64_fma"]["ops_per_s"],
+                     "peak_source": "FP64 FMA of peak_probe.cu, measured in this run"},
         "l2": "working set larger than L2 (GBs of Jacobians)",
     }
 
@@ -385,15 +407,66 @@ def run_adjoint(args, dev):
     qr_ms = float(phase_ms[md.PHASES.index("qr")]) / reps
     out = {"workload": acfg.name, "gradients_per_s": 1e3 / ms, "ms_per_gradient": ms,
            "roofline": {"bound": "alu", "fp64_ops_per_gradient": counts["fp64_ops"],
-                        "frac": counts["fp64_ops"] / (ms * 1e-3) / FP64_PEAK_OPS,
+                        "frac": counts["fp64_ops"] / (ms * 1e-3) / PEAKS["fp64_fma"]["ops_per_s"],
                         "dominant_kernel": "qr",
-                        "qr_frac": counts["qr_fp64_ops"] / (qr_ms * 1e-3) / FP64_PEAK_OPS if qr_ms > 0 else None,
-                        "peak": FP64_PEAK_OPS / 1e12, "unit": "FP64 Tops/s",
+                        "qr_frac": counts["qr_fp64_ops"] / (qr_ms * 1e-3) / PEAKS["fp64_fma"]["ops_per_s"]
+                        if qr_ms > 0 else None,
+                        "peak": PEAKS["fp64_fma"]["ops_per_s"] / 1e12, "unit": "FP64 Tops/s",
                         "note": "FP64-equivalent: the md algorithms' FP64 operation count against the FP64 "
                                 "pipe; the QR, the evaluation and the solve run in integer limbs"},
            "gradient_entries": int(grad.numel() // acfg.K), "loss_leading": float(loss[0]),
            "phases_ms_per_gradient": {p: float(v) / reps for p, v in zip(md.PHASES, phase_ms)}}
     nw.close()
+    return out
+
+
+def measure_peaks():
+    """The FP64 and integer pipe peaks of this GPU, measured now."""
+    from paper_2301_12659_gb300 import peaks
+    PEAKS.clear()
+    PEAKS.update(peaks.measure())
+    return PEAKS
+
+
+def phase_rooflines(cfg, s, ms_per_step):
+    """Per phase (evaluation, QR of A0, forward substitution): the method's
+    md multiply-adds per step (flops.method_counts; the QR counts its
+    (2/3) n^3 multiply-adds, not the inverse this library forms from it),
+    their rate, the paper-convention GFLOPS (Table 2 multiplication
+    weights) and the fraction of the measured integer pipe peak (integer
+    instructions per md multiply-add from ncu; where no figure exists for
+    the limb count, the FP64-equivalent fraction of the measured FP64 peak
+    is the main one)."""
+    m = F.method_counts(s.monomial_sizes(), s.n, s.D, s.C)
+    work = {"evaluate": m["evaluate"], "qr": m["qr"], "forward": m["updates"] + m["qhb"] + m["bs"]}
+    kernel = {"evaluate": "ed_kernel", "qr": "qr_kernel", "forward": "fsub_kernel"}
+    real = m["real_factor"]
+    cost = XF_INT_OPS_PER_FMA.get(cfg.K)
+    fp64_per_fma = F.md_ops(cfg.K)["acc_fma"]
+    int_peak = PEAKS["int_mix"]["ops_per_s"]
+    fp64_peak = PEAKS["fp64_fma"]["ops_per_s"]
+    out = {}
+    for p, w in work.items():
+        t = ms_per_step[p] * 1e-3
+        if t <= 0:
+            continue
+        rate = w * real / t  # real md multiply-adds per second
+        fp64 = {"achieved": rate * fp64_per_fma / 1e12, "peak": fp64_peak / 1e12, "unit": "FP64 Tops/s",
+                "frac": rate * fp64_per_fma / fp64_peak,
+                "note": f"{fp64_per_fma} FP64 operations per md multiply-add of md.cuh's algorithms"}
+        r = {"bound": "alu", "kernel": kernel[p], "md_fma_per_step": w * real, "md_fma_per_s": rate,
+             "paper_gflops": w * real * F.PAPER_MUL_COST[cfg.K] / t / 1e9, "fp64_equivalent": fp64}
+        if cost:
+            r.update({"achieved": rate * cost / 1e12, "peak": int_peak / 1e12, "unit": "integer Tops/s",
+                      "frac": rate * cost / int_peak,
+                      "peak_source": "IMAD/LOP3 mix of peak_probe.cu, measured in this run",
+                      "work": f"method md multiply-adds x {cost:g} integer instructions per multiply-add "
+                              "(ncu, ed_kernel)"})
+        else:
+            r.update({k: fp64[k] for k in ("achieved", "peak", "unit", "frac")})
+            r["peak_source"] = "FP64 FMA of peak_probe.cu, measured in this run"
+            r["work"] = "method md multiply-adds x FP64 operations per multiply-add (an equivalent)"
+        out[p] = r
     return out
 
 
@@ -410,6 +483,7 @@ def run_ours(args, cfg):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    measure_peaks()
     s, xstar, x0 = wl.planted_system(cfg)
     s.cst = None
     nw = md.Newton(s)
@@ -492,44 +566,25 @@ def run_ours(args, cfg):
     e2e_value = world * cfg.steps / (statistics.median(e2e_ms) * 1e-3)
     nbytes = x0.nbytes
 
-    # roofline of the phase with the largest share of device time
+    # roofline of the phase with the largest share of device time, in the
+    # method's work (md multiply-adds, flops.method_counts) against the
+    # measured peak of the pipe it runs on
     counts = F.step_counts(s.monomial_sizes(), s.n, s.D, s.K, s.C)
     steps_timed = args.steps
     share = {p: float(ms) for p, ms in zip(md.PHASES, phase_ms)}
-    md_fma = {"evaluate": counts["evaluate"]["md_fma"], "qr": counts["solve"]["qr_md_fma"],
-              "forward": counts["solve"]["forward_md_fma"]}
-    dom = max(md_fma, key=lambda p: share[p])
-    dom_launch_ms = share[dom] / steps_timed
-    eval_ms = share["evaluate"] / steps_timed
-    unit_cost = XF_INT_OPS_PER_FMA.get(cfg.K) if cfg.C == 1 else None
-    if unit_cost:
-        # algorithmic md multiply-adds x integer instructions per multiply-add
-        per_phase_ops = {p: v * unit_cost for p, v in md_fma.items()}
-        peak, unit = INT_PEAK_OPS, "int Tops/s"
-        peak_source = "derived: 152 SMs x 64 integer lanes/clk/SM (measured IMAD/LOP3) x 2070 MHz"
-        work = f"{md_fma[dom]} md multiply-adds x {unit_cost:g} integer instructions each (ncu, ed_kernel)"
-    else:
-        # no measured integer cost for these limbs: the FP64 operations the md
-        # algorithms would take, against the FP64 pipe (an equivalent, which
-        # exceeds 1 where the kernels run in integer limbs instead)
-        per_phase_ops = {"evaluate": counts["evaluate"]["fp64_ops"], "qr": counts["solve"]["qr_fp64_ops"],
-                         "forward": counts["solve"]["forward_fp64_ops"]}
-        peak, unit = FP64_PEAK_OPS, "FP64-equivalent Tops/s"
-        peak_source = "derived: 152 SMs x 1.684 FP64 lanes/clk/SM (measured) x 2070 MHz"
-        work = ("FP64 operations of the md algorithms (flops.py); the evaluation, QR and forward "
-                "substitution run in integer limbs, so this is an equivalent, not a pipe fraction")
-    achieved = per_phase_ops[dom] / (dom_launch_ms * 1e-3)
+    roof = phase_rooflines(cfg, s, {p: share[p] / steps_timed for p in md.PHASES})
+    dom = max(("evaluate", "qr", "forward"), key=lambda p: share[p])
+    main_roof = dict(roof[dom])
+    main_roof["traffic"] = NCU_TRAFFIC.get((cfg.name, dom))
     line = {
         "metric": metric_of(cfg), "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(cfg), "data": "synthetic",
         "config": config_dict(cfg, args),
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": peak / 1e12,
-                     "unit": unit, "frac": achieved / peak,
-                     "traffic": NCU_TRAFFIC.get((cfg.name, dom)),
-                     "peak_source": peak_source, "ops_per_launch": per_phase_ops[dom], "work": work},
+        "roofline": main_roof,
         "phases_ms_per_step": {p: share[p] / steps_timed for p in md.PHASES},
-        "evaluate_roofline_frac": (per_phase_ops["evaluate"] / (eval_ms * 1e-3)) / peak if eval_ms > 0 else None,
+        "phase_rooflines": roof,
+        "peaks": PEAKS,
         "step_fp64_ops": counts["fp64_ops"], "step_paper_flops": counts["paper_flops"],
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": nbytes / cfg.steps,
                 "d2h_bytes_per_step": (nbytes + 24 * cfg.steps) / cfg.steps,
@@ -548,8 +603,14 @@ def run_ours(args, cfg):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, cores = oracle_sample(cfg, args.cpu_sample_steps, args.cpu_threads)
         line["cpu_baseline"] = {"value": args.cpu_sample_steps / dt, "unit": "steps/s", "cores": cores,
-                                "kind": "oracle",
+                                "kind": "oracle", "host_cpus": os.cpu_count(),
                                 "sample": f"{args.cpu_sample_steps} oracle Newton steps from the start series"}
+        if args.cpu_single_thread:
+            dt1 = oracle_single_thread_step(cfg)
+            line["cpu_baseline"]["single_thread"] = {
+                "value": 1.0 / dt1, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                "sample": "1 oracle Newton step at the series after 5 steps (a late step, whose full-width "
+                          "coefficients make it the costliest of a solve) on one host thread"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     nw.close()
@@ -568,6 +629,7 @@ def run_ed_context(args):
     import torch
     from paper_2301_12659_gb300 import mdnewton as md
 
+    measure_peaks()
     n, d, K = 1024, 63, 8
     D = d + 1
     s, x = wl.one_column_system(n, d, K)
@@ -595,14 +657,88 @@ def run_ed_context(args):
                        "64 coefficients, real octo double; evaluation and differentiation only",
             "ms": ms, "paper_convention_gflops": paper_flops / (ms * 1e-3) / 1e9,
             "paper_table5_gflops_order64": {"P100": 554.654, "V100": 1658.382, "A100": 2568.016},
-            "fp64_ops": ops, "fp64_frac": ops / (ms * 1e-3) / FP64_PEAK_OPS,
+            "fp64_ops": ops, "fp64_frac": ops / (ms * 1e-3) / PEAKS["fp64_fma"]["ops_per_s"],
             "check_f0_leading": float(f[0, 0, n - 1, 0])}
     print(json.dumps(line), flush=True)
     nw.close()
 
 
+# Table 4 of the paper (V100, octo double, n = 1024, 64 coefficients, 24 Newton
+# steps): kernel seconds by kind and the wall time, one and two columns.
+TABLE4_V100 = {
+    1: {"convolutions": 121.386, "qr": 24.451, "qhb": 5.849, "bs": 17.053, "updates": 111.474,
+        "residuals": 125.122, "all_kernels": 405.334, "wall": 1129.794},
+    2: {"convolutions": 244.535, "qr": 24.123, "qhb": 6.139, "bs": 17.884, "updates": 124.080,
+        "residuals": 137.963, "all_kernels": 554.723, "wall": 1808.480},
+}
+
+
+def run_table4(args):
+    """The paper's Table 4 runs: Newton on the one- and two-column systems of
+    Section 3 at n = 1024 with 64 coefficients in real octo double, 24 steps
+    with staggered orders (6 steps on x_0 alone, each with its QR of A_0,
+    then 1 -> 2 -> 4 -> 7 -> ... -> 64 coefficients reusing the last QR:
+    Sections 4 and 5.3).  Device seconds per phase (mdn_profile) in the
+    paper's kernel categories, beside its V100 row (context: another GPU)."""
+    import torch
+    from paper_2301_12659_gb300 import mdnewton as md
+
+    torch.cuda.set_device(dist_info()[2])
+    measure_peaks()
+    out = {"context": "the paper's Table 4 workloads: one- and two-column systems of Section 3, n = 1024, "
+                      "64 coefficients, real octo double, 24 Newton steps with staggered orders and the QR once",
+           "runs": []}
+    steps, first = 24, 6
+    for columns in (1, 2):
+        s, x0 = wl.section3_system(1024, 63, 8, columns)
+        nw = md.Newton(s)
+        nw.set_stagger(first)
+        x0d = torch.as_tensor(x0, device="cuda")
+        nw.set_series(x0d)
+        md.mdn_newton(nw.ctx, 2, 0.0)  # warm-up (module loads, first launches)
+        torch.cuda.synchronize()
+        nw.set_series(x0d)
+        md.mdn_profile(nw.ctx, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        st, done, hist = md.mdn_newton(nw.ctx, steps, 0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        _, phase_ms, launches = md.mdn_profile(nw.ctx, 0)
+        alpha = s.meta["alpha"]
+        x = nw.series()[0, 0].cpu().numpy()
+        fact = np.array([float(np.prod(np.arange(1, j + 1))) for j in range(s.D)])
+        ref = alpha[:, None] ** np.arange(s.D)[None, :] / fact[None, :]
+        ph = {p: float(v) / 1e3 for p, v in zip(md.PHASES, phase_ms)}
+        out["runs"].append({
+            "columns": columns, "status": md.STATUS.get(st, st), "steps": done,
+            "device_s": e0.elapsed_time(e1) / 1e3, "wall_s": wall,
+            "newton_steps_per_s": done / (e0.elapsed_time(e1) / 1e3),
+            "phases_s": {"convolutions (evaluate + assemble)": ph["evaluate"] + ph["assemble"],
+                         "qr (QR of A_0 with Q^H and R^{-1}, forming A_0^{-1})": ph["qr"],
+                         "updates + residuals (forward substitution, fused monitor)": ph["forward"],
+                         "update of x and norms": ph["update"]},
+            "gpu_launches": int(np.sum(launches)),
+            "final_norms": [float(v) for v in hist[-1]],
+            "leading_limb_error_vs_exp_alpha_t": float(np.max(np.abs(x - ref))),
+            "paper_v100_seconds": TABLE4_V100[columns],
+        })
+        nw.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.table4:
+        run_table4(args)
+        return
+    if args.peaks:
+        import torch
+        torch.cuda.set_device(dist_info()[2])
+        print(json.dumps({"peaks": measure_peaks()}), flush=True)
+        return
     if args.ed_context:
         run_ed_context(args)
         return

@@ -107,6 +107,38 @@ def solve_counts(n: int, D: int, K: int, C: int) -> dict:
     }
 
 
+def method_counts(sizes, n: int, D: int, C: int) -> dict:
+    """The method's md multiply-adds per Newton step, phase by phase, as the
+    paper structures the step (independent of how this library forms them):
+
+    * evaluation and differentiation (Section 5.1): 3k-3 truncated products
+      per monomial of k >= 2 variables, D(D+1)/2 multiply-adds each;
+    * Householder QR of A0 (Section 5.3): sum over the columns j of
+      (n-j) for the pivot norm and 2(n-j) per later column (w = v^H y and
+      y -= tau w v), (2/3) n^3 + O(n^2) multiply-adds, i.e. (4/3) n^3 md
+      operations;
+    * per stage k, Q^H b (n(n+1): per reflector j a dot product and an
+      update over rows j..n-1) and the back substitution with R (n(n+1)/2);
+    * the right hand side updates sum_{j>=1} A_j dx_{k-j} (n^2 per block,
+      D(D-1)/2 blocks in all);
+    * the residual b - A dx of the full block Toeplitz system
+      (n^2 D(D+1)/2).
+    Complex data count complex multiply-adds (four real ones each)."""
+    sizes = np.asarray(sizes)
+    nprod = int(sum(products_per_monomial(int(k)) for k in sizes))
+    qr = sum((n - j) + 2 * (n - j) * (n - j - 1) for j in range(n))
+    out = {
+        "evaluate": nprod * (D * (D + 1) // 2),
+        "qr": qr,
+        "qhb": D * n * (n + 1),
+        "bs": D * (n * (n + 1) // 2),
+        "updates": n * n * (D * (D - 1) // 2),
+        "residual": n * n * (D * (D + 1) // 2),
+    }
+    out["real_factor"] = 4 if C == 2 else 1
+    return out
+
+
 def step_counts(sizes, n: int, D: int, K: int, C: int) -> dict:
     e = ed_counts(sizes, D, K, C)
     s = solve_counts(n, D, K, C)

@@ -59,3 +59,61 @@ def test_complex_counts_are_four_real_products(K):
     r, c = flops.cmd_ops(K, 1), flops.cmd_ops(K, 2)
     assert c["acc_fma"] == 4 * r["acc_fma"]
     assert c["acc_add"] == 2 * r["acc_add"]
+
+
+def _householder_count(n):
+    """Multiply-adds of a plain Householder QR of an n x n matrix, counted
+    while it runs (pure Python, no formula): the pivot norm over rows j..n-1,
+    then for every later column the dot product v^H y and the update
+    y -= tau w v over the same rows."""
+    import random
+    rnd = random.Random(n)
+    a = [[rnd.uniform(-1, 1) + (n if i == j else 0) for j in range(n)] for i in range(n)]
+    count = 0
+    for j in range(n):
+        norm2 = 0.0
+        for i in range(j, n):
+            norm2 += a[i][j] * a[i][j]
+            count += 1
+        alpha = -norm2 ** 0.5 if a[j][j] >= 0 else norm2 ** 0.5
+        v = [0.0] * n
+        for i in range(j, n):
+            v[i] = a[i][j]
+        v[j] -= alpha
+        vv = sum(v[i] * v[i] for i in range(j, n))
+        for c in range(j + 1, n):
+            w = 0.0
+            for i in range(j, n):
+                w += v[i] * a[i][c]
+                count += 1
+            for i in range(j, n):
+                a[i][c] -= 2.0 * w / vv * v[i]
+                count += 1
+        a[j][j] = alpha
+        for i in range(j + 1, n):
+            a[i][j] = 0.0
+    return count
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 16, 64])
+def test_method_qr_count_is_a_householder_qr(n):
+    """The QR's method work is the multiply-adds a Householder QR performs,
+    (2/3) n^3 + O(n^2) of them ((4/3) n^3 md operations, multiplications and
+    additions), counted by running one."""
+    assert flops.method_counts([1], n, 4, 1)["qr"] == _householder_count(n)
+    if n == 64:
+        assert abs(flops.method_counts([1], n, 4, 1)["qr"] / n ** 3 - 2 / 3) < 0.03
+
+
+def test_method_forward_counts_by_enumeration():
+    """Updates, Q^H b, back substitution and the block Toeplitz residual,
+    counted by enumerating the products of each stage."""
+    n, D = 5, 7
+    upd = sum(n * n for k in range(D) for j in range(1, k + 1))
+    res = sum(n * n for k in range(D) for j in range(k + 1))
+    qhb = sum(2 * (n - j) for _ in range(D) for j in range(n))  # v^H b, then b -= tau w v
+    bs = sum(sum(n - i for i in range(n)) for _ in range(D))
+    m = flops.method_counts([2, 3], n, D, 1)
+    assert m["updates"] == upd and m["residual"] == res and m["bs"] == bs
+    assert m["qhb"] == qhb
+    assert m["evaluate"] == (1 + 1) * 0 + (3 + 6) * D * (D + 1) // 2

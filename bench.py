@@ -53,7 +53,7 @@ from paper_2301_12659_gb300 import workloads as wl  # noqa: E402
 # one real md multiply-add in integer limbs costs this many integer thread
 # instructions (operand conversions and the accumulator included), measured
 # with ncu on ed_kernel (profiles/ed_kernel_int_per_fma.md):
-XF_INT_OPS_PER_FMA = {4: 406.6}
+XF_INT_OPS_PER_FMA = {2: 169.6, 4: 406.6, 8: 957.7}
 NUM_SMS = 152
 PEAKS = {}
 
@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=70)
     ap.add_argument("--warmup", type=int, default=7)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="qd-real-n64-d31", choices=sorted(wl.CONFIGS))
+    ap.add_argument("--config", default="qd-real-n64-d31", choices=sorted({**wl.CONFIGS, **wl.EXTRA_CONFIGS}))
     ap.add_argument("--e2e-solves", type=int, default=5)
     ap.add_argument("--cpu-sample-steps", type=int, default=14)
     ap.add_argument("--cpu-threads", type=int, default=0,
@@ -91,7 +91,8 @@ def parse():
                     help="also time the batched workload (4096 quad double systems) and the same systems one by one")
     ap.add_argument("--adjoint", default="on", choices=["on", "off"],
                     help="also time the adjoint gradient of the double double n=64, d=31 workload")
-    ap.add_argument("--one-by-one-sample", type=int, default=48)
+    ap.add_argument("--one-by-one-sample", type=int, default=512,
+                    help="systems of the batch solved one by one (stratified by size class; 0: all)")
     ap.add_argument("--batch-count", type=int, default=0,
                     help="systems of the batched workload (0: all 4096; fewer for profiling captures)")
     ap.add_argument("--staggered", default="on", choices=["on", "off"],
@@ -108,9 +109,9 @@ def parse():
 # capture of the unchanged kernels (profiles/ncu_qr_ed_fsub_qd-real-n64-d31.md);
 # absent entries report null.
 NCU_TRAFFIC = {
-    ("qd-real-n64-d31", "qr"): 603904 + 8448,
-    ("qd-real-n64-d31", "evaluate"): 1294848,
-    ("qd-real-n64-d31", "forward"): 4622592 + 42368,
+    ("qd-real-n64-d31", "qr"): 540544,
+    ("qd-real-n64-d31", "evaluate"): 1294976,
+    ("qd-real-n64-d31", "forward"): 4646400 + 27264,
 }
 
 
@@ -300,7 +301,8 @@ def run_batched(args, dev):
         worst = max(worst, float(np.max(np.abs(xs[q][0] - items[q][1][0]))))
     cst = b.unpack(b.cst)
     # one by one, on a stratified sample
-    idx = autotune._stratified(systems, args.one_by_one_sample, seed=1)
+    idx = (list(range(len(systems))) if args.one_by_one_sample <= 0 or args.one_by_one_sample >= len(systems)
+           else autotune._stratified(systems, args.one_by_one_sample, seed=1))
     per_class = {}
     for q in idx:
         s = systems[q]
@@ -326,6 +328,9 @@ def run_batched(args, dev):
     for q, s in enumerate(systems):
         ops += float(steps[q]) * F.step_counts(s.monomial_sizes(), s.n, s.D, s.K, s.C)["fp64_ops"]
     one_ms = sum(counts[c] * float(np.mean(v)) for c, v in per_class.items())
+    spread = {f"n={c[0]},d={c[1]}": {"in_batch": counts[c], "timed": len(v), "ms_mean": float(np.mean(v)),
+                                     "ms_min": float(np.min(v)), "ms_max": float(np.max(v))}
+              for c, v in sorted(per_class.items())}
     b.close()
     return {
         "workload": bcfg.name, "systems": len(items), "solves_per_s": len(items) / (ms * 1e-3),
@@ -334,8 +339,10 @@ def run_batched(args, dev):
         "updates": int(np.sum(steps)), "converged": int(np.sum(flags == md.BATCH_CONVERGED)),
         "max_leading_limb_error_vs_plant_sampled": worst, "gpu_launches_per_batch": 1,
         "one_by_one": {"solves_per_s": len(items) / (one_ms * 1e-3), "ms_total_estimate": one_ms,
-                       "sample": f"{len(idx)} systems stratified by (n, d), each through mdn_newton for the "
-                                 "number of updates the batch applied to it, scaled by the class counts"},
+                       "sample": f"{len(idx)} of the {len(items)} systems (stratified by (n, d)), each through "
+                                 "mdn_newton for the number of updates the batch applied to it; class means "
+                                 "scaled by the class counts",
+                       "per_class": spread},
         "speedup_vs_one_by_one": one_ms / ms, "generate_s": gen_s,
         "roofline": {"bound": "alu", "kernel": "batch_kernel", "ops_per_launch": ops,
                      "achieved": ops / (ms * 1e-3) / 1e12, "peak": PEAKS["fp64_fma"]["ops_per_s"] / 1e12,
@@ -742,7 +749,7 @@ def main():
     if args.ed_context:
         run_ed_context(args)
         return
-    cfg = wl.CONFIGS[args.config]
+    cfg = {**wl.CONFIGS, **wl.EXTRA_CONFIGS}[args.config]
     if args.impl == "reference":
         run_reference(args, cfg)
     else:

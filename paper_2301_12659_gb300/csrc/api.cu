@@ -700,8 +700,9 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* 
 static int qr_blocks(const mdn_ctx* ctx) { return ctx->large_qr ? ctx->num_sms : qr_blocks_for(ctx->n); }
 // Kernel launches of A_0 and its QR: two for A_0, the epoch bump, then the
 // dataflow kernel and W, or the column-by-column sequence (initialisation,
-// a pivot and an update launch per column, the back substitution).
-static int qr_launches(const mdn_ctx* ctx) { return 3 + (ctx->large_qr ? 2 * ctx->n + 2 : 2); }
+// the first pivot, an update launch per column that also forms the next
+// pivot, the back substitution).
+static int qr_launches(const mdn_ctx* ctx) { return 3 + (ctx->large_qr ? ctx->n + 3 : 2); }
 
 // Forward substitution for dx with right hand side sgn * rhs: stage 0 alone
 // (dx_0 = W r_0, and x_0 + dx_0 into the xnext0 buffer when x is given), the

@@ -1133,7 +1133,7 @@ __global__ void qrg_init_kernel(QrParams p) {
 }
 
 template <int K, int C>
-__global__ void qrg_pivot_kernel(QrParams p, int j) {
+__device__ void qrg_pivot(const QrParams& p, int j) {
   using namespace xfn;
   constexpr int W = xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
@@ -1231,6 +1231,16 @@ __global__ void qrg_pivot_kernel(QrParams p, int j) {
 }
 
 template <int K, int C>
+__global__ void qrg_pivot_kernel(QrParams p, int j) {
+  qrg_pivot<K, C>(p, j);
+}
+
+// Reflector j applied to the later columns of Aw and to the columns of Yw.
+// Look-ahead: warp 0 takes column j+1 alone and forms the pivot scalars of
+// reflector j+1 right after its update, while the other warps update the
+// remaining columns; the next launch (reflector j+1) then needs no pivot
+// launch of its own.
+template <int K, int C>
 __global__ void qrg_apply_kernel(QrParams p, int j) {
   using namespace xfn;
   constexpr int W = xf_words_t<K>::value;
@@ -1247,7 +1257,10 @@ __global__ void qrg_apply_kernel(QrParams p, int j) {
   xld<W, C>(p.salpha, p.n, j, sa);
   xld<W, C>(p.v0, p.n, j, v0);
   const int head = acc_extra_head(C * (n - j));
-  for (long long t = w0; t < na + n; t += nw) {
+  // warp 0: column j+1 (t = 0) then the pivot of j+1; the others: t >= 1
+  const long long tfirst = (na > 0 && nw > 1) ? (w0 == 0 ? 0 : w0) : w0;
+  const long long tstep = (na > 0 && nw > 1) ? (w0 == 0 ? na + n : nw - 1) : nw;
+  for (long long t = tfirst; t < na + n; t += tstep) {
     uint64_t* Y = t < na ? p.Aw : p.Yw;
     const long long ycol = (t < na ? (long long)(j + 1 + t) : (long long)(t - na)) * n;
     // dot = x_j^H y over rows j..n-1
@@ -1284,6 +1297,7 @@ __global__ void qrg_apply_kernel(QrParams p, int j) {
     }
     __syncwarp();
   }
+  if (w0 == 0 && na > 0 && nw > 1) qrg_pivot<K, C>(p, j + 1);
 }
 
 template <int K, int C>
@@ -1874,9 +1888,10 @@ template <int K, int C>
 cudaError_t launch_qr_large(const QrParams& p, cudaStream_t s) {
   const int n = p.n;
   qrg_init_kernel<K, C><<<grid_for((long long)n * n, 256), 256, 0, s>>>(p);
+  qrg_pivot_kernel<K, C><<<1, 32, 0, s>>>(p, 0);
   for (int j = 0; j < n; ++j) {
-    qrg_pivot_kernel<K, C><<<1, 32, 0, s>>>(p, j);
-    const long long cols = (long long)(n - 1 - j) + n;  // a warp per column
+    // a warp per column, at least two warps (the first forms the next pivot)
+    const long long cols = (long long)(n - 1 - j) + n + 1;
     qrg_apply_kernel<K, C><<<grid_for(cols * 32, 128), 128, 0, s>>>(p, j);
   }
   qrg_bsub_kernel<K, C><<<(n + 3) / 4, 128, 0, s>>>(p);

@@ -399,6 +399,32 @@ XF_FN void xf_pack(uint64_t (&g)[W + 1], int e, int s, xf<W>& r) {
   r.s = z ? 0 : s;
 }
 
+// xf_pack for a g whose leading bit is bit 63 or 62 of its top word (the
+// product of two mantissas in [1, 2), or a sum without cancellation): a
+// one-bit normalisation instead of the general count and shift.
+template <int W>
+XF_FN void xf_pack_near(const uint64_t (&g)[W + 1], int e, int s, xf<W>& r) {
+  const bool top = (g[W] >> 63) != 0ULL;
+#pragma unroll
+  for (int i = 0; i < W; ++i) r.m[i] = top ? g[i + 1] : ((g[i + 1] << 1) | (g[i] >> 63));
+  r.e = top ? e : e - 1;
+  r.s = s;
+}
+
+// Whether every lane of the warp (on the host: this value) can take the
+// one-bit normalisation: the leading bit of g sits in bit 63 or 62 of its
+// top word.  On the device the decision is warp-uniform, so a warp whose
+// lanes disagree takes the general path together.
+template <int W>
+XF_FN bool pack_near_ok(const uint64_t (&g)[W + 1]) {
+  const bool near = (g[W] >> 62) != 0ULL;
+#if defined(__CUDA_ARCH__)
+  return __all_sync(__activemask(), near);
+#else
+  return near;
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // arithmetic
 // ---------------------------------------------------------------------------
@@ -460,7 +486,10 @@ XF_FN void xf_add(const xf<W>& a, const xf<W>& b, xf<W>& r) {
   const bool carry = g[W + 1] != 0ULL;
 #pragma unroll
   for (int i = 0; i <= W; ++i) h[i] = carry ? fshr(g[i], g[i + 1], 1) : g[i];
-  xf_pack<W>(h, x.e + (carry ? 1 : 0), x.s, r);
+  // a sum of like signs, and a difference that cancels at most one bit, has
+  // its leading bit in bit 63 or 62 of h[W]
+  if (pack_near_ok<W>(h)) xf_pack_near<W>(h, x.e + (carry ? 1 : 0), x.s, r);
+  else xf_pack<W>(h, x.e + (carry ? 1 : 0), x.s, r);
 }
 
 template <int W>
@@ -503,7 +532,7 @@ XF_FN void xf_mul(const xf<W>& a, const xf<W>& b, xf<W>& r) {
     xf_zero(r);
     return;
   }
-  xf_pack<W>(h, a.e + b.e + 1, a.s ^ b.s, r);
+  xf_pack_near<W>(h, a.e + b.e + 1, a.s ^ b.s, r);
 }
 
 // r = a >> s for s >= 0 (N words, truncated; s >= 64N gives zero)

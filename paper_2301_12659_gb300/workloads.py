@@ -201,6 +201,13 @@ CONFIGS = {
 #: the gradient is taken with respect to every coefficient series.
 ADJOINT_CONFIG = PlantedConfig("dd-real-n64-d31-adjoint", 2, 1, 64, 31, 16, 2, 8, 64.0, 7, 1e-28, 4)
 
+#: The quad double recipe in the other precisions (the same system sizes),
+#: for per-precision measurements: double double and real octo double.
+EXTRA_CONFIGS = {
+    "dd-real-n64-d31": PlantedConfig("dd-real-n64-d31", 2, 1, 64, 31, 16, 2, 8, 64.0, 7, 1e-28, 4),
+    "od-real-n64-d31": PlantedConfig("od-real-n64-d31", 8, 1, 64, 31, 16, 2, 8, 64.0, 8, 1e-118, 7),
+}
+
 
 def small_config(K: int, C: int, n: int, d: int, mono_per_eq: int = 3, kmin: int = 1, kmax: int = 3,
                  diag: float = None, steps: int = 6, tol: float = None, index: int = 100) -> PlantedConfig:

@@ -322,11 +322,14 @@ def run_batched(args, dev):
     counts = {}
     for s in systems:
         counts[(s.n, s.d)] = counts.get((s.n, s.d), 0) + 1
-    # algorithmic FP64 operations of the updates applied (one evaluation, QR
-    # and forward substitution per update; the stopping evaluations not counted)
-    ops = 0.0
+    # algorithmic work of the updates applied (one evaluation, QR and forward
+    # substitution per update; the stopping evaluations not counted): FP64
+    # operations of md.cuh's algorithms, and the method's md multiply-adds
+    ops, mfma = 0.0, 0.0
     for q, s in enumerate(systems):
         ops += float(steps[q]) * F.step_counts(s.monomial_sizes(), s.n, s.D, s.K, s.C)["fp64_ops"]
+        mc = F.method_counts(s.monomial_sizes(), s.n, s.D, s.C)
+        mfma += float(steps[q]) * mc["real_factor"] * (mc["evaluate"] + mc["qr"] + mc["updates"] + mc["qhb"] + mc["bs"])
     one_ms = sum(counts[c] * float(np.mean(v)) for c, v in per_class.items())
     spread = {f"n={c[0]},d={c[1]}": {"in_batch": counts[c], "timed": len(v), "ms_mean": float(np.mean(v)),
                                      "ms_min": float(np.min(v)), "ms_max": float(np.max(v))}
@@ -344,10 +347,18 @@ def run_batched(args, dev):
                                  "scaled by the class counts",
                        "per_class": spread},
         "speedup_vs_one_by_one": one_ms / ms, "generate_s": gen_s,
-        "roofline": {"bound": "alu", "kernel": "batch_kernel", "ops_per_launch": ops,
-                     "achieved": ops / (ms * 1e-3) / 1e12, "peak": PEAKS["fp64_fma"]["ops_per_s"] / 1e12,
-                     "unit": "FP64 Tops/s", "frac": ops / (ms * 1e-3) / PEAKS["fp64_fma"]["ops_per_s"],
-                     "peak_source": "FP64 FMA of peak_probe.cu, measured in this run"},
+        "roofline": {"bound": "alu", "kernel": "batch_kernel", "md_fma_per_launch": mfma,
+                     "md_fma_per_s": mfma / (ms * 1e-3),
+                     "achieved": mfma * XF_INT_OPS_PER_FMA[bcfg.K] / (ms * 1e-3) / 1e12,
+                     "peak": PEAKS["int_mix"]["ops_per_s"] / 1e12, "unit": "integer Tops/s",
+                     "frac": mfma * XF_INT_OPS_PER_FMA[bcfg.K] / (ms * 1e-3) / PEAKS["int_mix"]["ops_per_s"],
+                     "peak_source": "IMAD/LOP3 mix of peak_probe.cu, measured in this run",
+                     "work": "the method's md multiply-adds of the updates applied x integer instructions per "
+                             "multiply-add (ncu, ed_kernel); the products of the evaluation run in integer limbs, "
+                             "the QR and the forward substitution in FP64 md operations",
+                     "fp64_equivalent": {"ops_per_launch": ops, "achieved": ops / (ms * 1e-3) / 1e12,
+                                         "peak": PEAKS["fp64_fma"]["ops_per_s"] / 1e12, "unit": "FP64 Tops/s",
+                                         "frac": ops / (ms * 1e-3) / PEAKS["fp64_fma"]["ops_per_s"]}},
         "l2": "working set larger than L2 (GBs of Jacobians)",
     }
 

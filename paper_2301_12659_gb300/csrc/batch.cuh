@@ -67,9 +67,17 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
 //   d_1 = c B_{k-1}                  (k >= 2)
 //   d_q = F_{q-1} B_{k-q}            q = 2..k-1
 // and d_k = F_{k-1} (no product): 3k-3 products for k >= 2, one for k = 1.
+// Shared memory of the evaluation's products in integer limbs (K >= 2): per
+// warp its G lane groups' operands, 2 C D extended floats each (G D <= 64).
+template <int K, int C>
+__host__ __device__ inline size_t batch_smem_bytes(int threads) {
+  if (K < 2) return 0;
+  return (size_t)(threads / 32) * 2 * C * 64 * sizeof(xfn::xf<xfn::xf_words_t<K>::value>);
+}
+
 template <int K, int C>
 __device__ void batch_evaluate(const BatchParams& p, const BatchSys& s, const BWork& w, double* f, long long Nf,
-                               bool want_A) {
+                               bool want_A, unsigned char* smem) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int n = s.n, D = s.D;
   const int P = (D + 1) / 2, G = 32 / P;
@@ -136,7 +144,16 @@ __device__ void batch_evaluate(const BatchParams& p, const BatchSys& s, const BW
             b = B(k - qd);
             o = Dp(qd);
           }
-          series_product<K, C>(a, b, o, t, D);
+          if constexpr (K >= 2) {
+            // operands converted once into shared memory, one fixed-point
+            // accumulator per coefficient (the evaluation kernel's product)
+            using X = xfn::xf<xfn::xf_words_t<K>::value>;
+            X* stage = reinterpret_cast<X*>(smem) + (warp * G + g) * (2 * C * D);
+            const unsigned gmask = (P >= 32 ? FULL : ((1u << P) - 1u)) << (g * P);
+            series_product_xf<K, C>(a, b, o, t, D, gmask, stage);
+          } else {
+            series_product<K, C>(a, b, o, t, D);
+          }
         }
         __syncwarp();
       }
@@ -425,6 +442,7 @@ __device__ void batch_forward(const BWork& w, int n, int D) {
 
 template <int K, int C>
 __global__ void batch_kernel(BatchParams p) {
+  extern __shared__ __align__(16) unsigned char batch_smem[];
   __shared__ int s_sys, s_flag;
   __shared__ unsigned long long s_max[3];
   const int tid = threadIdx.x, T = blockDim.x;
@@ -441,7 +459,7 @@ __global__ void batch_kernel(BatchParams p) {
     const long long N = (long long)s.n * s.D;
     double* xb = p.x + s.series_off;
     if (p.evaluate_only) {
-      batch_evaluate<K, C>(p, s, w, p.f_out + s.series_off, N, false);
+      batch_evaluate<K, C>(p, s, w, p.f_out + s.series_off, N, false, batch_smem);
       __syncthreads();
       if (tid == 0) {
         p.steps_out[si] = 0;
@@ -453,7 +471,7 @@ __global__ void batch_kernel(BatchParams p) {
     for (;;) {
       __syncthreads();  // every thread has read the norms of the last step
       if (tid < 3) s_max[tid] = 0ull;
-      batch_evaluate<K, C>(p, s, w, w.f, N, true);
+      batch_evaluate<K, C>(p, s, w, w.f, N, true, batch_smem);
       __syncthreads();
       // ||f||_inf, and a non-finite check of f
       unsigned long long fm = 0;
@@ -522,15 +540,33 @@ __global__ void batch_kernel(BatchParams p) {
 }
 
 template <int K, int C>
+static cudaError_t batch_smem_attr() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  // the kernel's static shared memory counts against the same per-block
+  // limit; larger blocks do not fit (occupancy 0)
+  size_t most = batch_smem_bytes<K, C>(1024);
+  if (most > (size_t)QR_SMEM_MAX - 1024) most = QR_SMEM_MAX - 1024;
+  const cudaError_t e = cudaFuncSetAttribute(batch_kernel<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <int K, int C>
 cudaError_t launch_batch(const BatchParams& p, int blocks, int threads, cudaStream_t s) {
-  batch_kernel<K, C><<<blocks, threads, 0, s>>>(p);
+  cudaError_t e = batch_smem_attr<K, C>();
+  if (e != cudaSuccess) return e;
+  batch_kernel<K, C><<<blocks, threads, batch_smem_bytes<K, C>(threads), s>>>(p);
   return cudaGetLastError();
 }
 
 template <int K, int C>
 int batch_occupancy(int threads) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<K, C>, threads, 0) != cudaSuccess) return 0;
+  if (batch_smem_attr<K, C>() != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<K, C>, threads,
+                                                    batch_smem_bytes<K, C>(threads)) != cudaSuccess)
+    return 0;
   return nb;
 }
 

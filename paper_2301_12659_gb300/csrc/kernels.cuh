@@ -831,8 +831,11 @@ __device__ __forceinline__ void qr_form_w(const QrParams& p, int j, const uint64
 
 // y -= tau_j w v_j over rows j..n-1 (needs the ref flag of reflector j).
 template <int K, int C>
+// With pub >= 0 (the column warp's last reflector, j = pub - 1), rows
+// pub..n-1 of the result, the column x_pub that its owner publishes next,
+// are also stored to Vm as they are formed.
 __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
-                                          const cxf<xfn::xf_words_t<K>::value, C>& w) {
+                                          const cxf<xfn::xf_words_t<K>::value, C>& w, int pub = -1) {
   constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
@@ -857,6 +860,10 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
     cxf_fma<false>(y2, ng, v2);
     xst<W, C>(y, n, i, yi);
     if (two) xst<W, C>(y, n, i2, y2);
+    if (pub >= 0) {
+      if (i >= pub) xst<W, C>(p.Vm, p.Nnn, (long long)i * n + pub, yi);
+      if (two && i2 >= pub) xst<W, C>(p.Vm, p.Nnn, (long long)i2 * n + pub, y2);
+    }
   }
   __syncwarp();
 }
@@ -892,15 +899,16 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
     if (!warp_wait(&fal[j], ep, p.spin_limit, p.status)) return;
     qr_form_w<K, C>(p, j, y, dot, w);
     if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
-    qr_update<K, C>(p, j, y, w);
+    qr_update<K, C>(p, j, y, w, j == c - 1 ? c : -1);
     if (lane == 0) xcopy<W, C>(y, n, j, p.Rm, p.Nnn, (long long)j * n + c);  // R[j][c] is final
     cxf<W, C> xv, q;
     xld<W, C>(y, n, j, xv);
     cxf_mul<true>(xv, xv, q);
     xf_sub(xN, q.re, xN);
   }
-  // publish x_c (rows c..n-1)
-  for (int i = c + lane; i < n; i += 32) xcopy<W, C>(y, n, i, p.Vm, p.Nnn, (long long)i * n + c);
+  // publish x_c (rows c..n-1; the last update stored them for c > 0)
+  if (c == 0)
+    for (int i = c + lane; i < n; i += 32) xcopy<W, C>(y, n, i, p.Vm, p.Nnn, (long long)i * n + c);
   warp_publish(&fcol[c], ep);
   // N = |x_c|^2 by downdating, recomputed when it is not positive or more
   // than 8 bits cancelled
@@ -911,21 +919,15 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
   //   |x_c| = N / sqrt(N),  s = x_cc / |x_cc| (1 if x_cc = 0),
   //   v_cc = x_cc + s|x_c|,  tau = 1 / (N + |x_c| |x_cc|),
   //   R_cc = -s|x_c|,  1 / R_cc = -conj(s) / |x_c|.
-  xf<W> xry, xal, xax0;
-  xf_rsqrt(xN, xry);
-  xf_mul(xN, xry, xal);
   cxf<W, C> x0;
   xld<W, C>(y, n, c, x0);
-  xf<W> sre, sim;  // s|x_c|
+  xf<W> xry, xal, xax0;
   xf<W> sgr, sgi;  // s
   bool neg = false;
   if constexpr (C == 1) {
     neg = x0.re.s != 0;
     xax0 = x0.re;
     xax0.s = 0;
-    sre = xal;
-    if (neg) xf_neg(sre);
-    xf_zero(sim);
   } else {
     xf<W> t1, t2, a2x, rx;
     xf_mul(x0.re, x0.re, t1);
@@ -942,6 +944,15 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
       xf_from_double(1.0, sgr);
       xf_zero(sgi);
     }
+  }
+  xf_rsqrt(xN, xry);
+  xf_mul(xN, xry, xal);
+  xf<W> sre, sim;  // s|x_c|
+  if constexpr (C == 1) {
+    sre = xal;
+    if (neg) xf_neg(sre);
+    xf_zero(sim);
+  } else {
     xf_mul(sgr, xal, sre);
     xf_mul(sgi, xal, sim);
   }

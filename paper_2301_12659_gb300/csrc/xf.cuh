@@ -848,17 +848,23 @@ XF_FN void xf_recip(const xf<W>& a, xf<W>& r) {
   r = y;
 }
 
-// r = 1 / sqrt(a), a > 0
+// the double seed of 1 / sqrt(a), a > 0: a = M 2^e with M in [1, 2); for
+// odd e take 2M 2^(e-1)
 template <int W>
-XF_FN void xf_rsqrt(const xf<W>& a, xf<W>& r) {
-  xf<W> y;
-  // a = M 2^e with M in [1, 2); for odd e take 2M 2^(e-1)
+XF_FN void xf_rsqrt_seed(const xf<W>& a, xf<W>& y) {
   const bool odd = (a.e & 1) != 0;
   double md = xf_mant_double(a);
   md = odd ? md * 2.0 : md;
   const int eh = (odd ? a.e - 1 : a.e) / 2;
   xf_from_double(drsqrt(md), y);
   y.e -= eh;
+}
+
+// r = 1 / sqrt(a), a > 0
+template <int W>
+XF_FN void xf_rsqrt(const xf<W>& a, xf<W>& r) {
+  xf<W> y;
+  xf_rsqrt_seed(a, y);
   newton_steps<true>(a, y);
   r = y;
 }

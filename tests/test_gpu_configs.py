@@ -132,35 +132,42 @@ def test_od_complex_n128_d63_newton_with_the_oracle_plant(md):
             assert b <= max(1e4 * a * a, cfg.tol), lead
 
 
-def test_od_complex_reduced_analogue_matches_the_oracle(md):
+@pytest.mark.parametrize("diag,tag", [(16.0, "16"), (128.0, "16d128")])
+def test_od_complex_reduced_analogue_matches_the_oracle(md, diag, tag):
     """The complex octo double recipe at n = 16 (32 monomials per equation of
-    2..16 of the 16 variables, 64 coefficients on the unit circle, diagonal
-    16 x_i): GPU Newton after 8 and 9 steps against the oracle's Newton
-    (stored by tests/golden/make_od_complex_golden.py) coefficient by
-    coefficient, and both against the plant: the GPU's error profile over
-    the coefficients follows the oracle's, so the late-coefficient floor is
-    the method's (conditioning), not the kernels'."""
+    2..16 of the 16 variables, 64 coefficients on the unit circle), with the
+    diagonal n x_i = 16 x_i or with the full workload's 128 x_i: GPU Newton
+    after 8 and 9 steps against the oracle's Newton (stored by
+    tests/golden/make_od_complex_golden.py) coefficient by coefficient, and
+    both against the plant.  The oracle's own error grows geometrically
+    with the coefficient index (the error propagation of Section 2); the
+    GPU's profile follows it, so the late-coefficient floor is the method's
+    (conditioning), not the kernels'."""
     from tests.golden.make_od_complex_golden import reduced_config
     g = _golden_od()
-    cfg = reduced_config()
+    if f"x{tag}_9" not in g:
+        pytest.skip(f"no oracle values for the reduced analogue {tag}")
+    cfg = reduced_config(diag)
     s, xstar, x0 = wl.planted_system(cfg)
-    s.cst = g["cst16"]
+    s.cst = g[f"cst{tag}"]
     nw = md.Newton(s)
     nw.set_series(x0)
     nw.newton(8)
     x8 = to_np(nw.series())
     nw.newton(1)
     x9 = to_np(nw.series())
-    for x, ref in ((x8, g["x16_8"]), (x9, g["x16_9"])):
-        e_gpu = mt.series_rel_error(x, xstar).max(axis=0)
+    for x, ref in ((x8, g[f"x{tag}_8"]), (x9, g[f"x{tag}_9"])):
         e_orc = mt.series_rel_error(ref, xstar).max(axis=0)
+        e_gpu = mt.series_rel_error(x, xstar).max(axis=0)
         # entry by entry against the oracle, at the larger of the bar and the
         # oracle's own distance to the plant (where conditioning limits both)
         d = mt.series_rel_error(x, ref)
         assert np.all(d <= np.maximum(cfg.tol, 1e3 * e_orc[None, :])), (d.max(axis=0), e_orc)
         # the same profile over the coefficients: within a factor 1e3 or below the bar
-        assert np.all((e_gpu <= np.maximum(1e3 * e_orc, cfg.tol))), (e_gpu, e_orc)
-    assert np.max(mt.series_rel_error(x9, g["x16_9"])[:, :16]) <= cfg.tol
+        assert np.all(e_gpu <= np.maximum(1e3 * e_orc, cfg.tol)), (e_gpu, e_orc)
+        # where the oracle meets the bar, the GPU does
+        ok = e_orc <= cfg.tol
+        assert np.all(e_gpu[ok] <= cfg.tol)
 
 
 def test_od_complex_n128_d63_late_updates(md):

@@ -152,8 +152,11 @@ __device__ __forceinline__ bool warp_wait(const unsigned* flag, unsigned ep, lon
   __syncwarp();
   return ok != 0;
 }
+// The warp barrier orders every lane's earlier stores before lane 0's
+// release store at GPU scope (the release is cumulative over what lane 0 has
+// observed), so a reader that acquires the flag sees them: one release
+// instead of a full fence in every lane.
 __device__ __forceinline__ void warp_publish(unsigned* flag, unsigned ep) {
-  __threadfence();
   __syncwarp();
   if ((threadIdx.x & 31) == 0) st_release(flag, ep);
   __syncwarp();

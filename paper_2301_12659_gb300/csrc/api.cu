@@ -181,7 +181,7 @@ struct Layout {
       o_eq_mon, o_pair_ptr, o_pair_slot, o_occ, o_counter, o_status, o_flags, o_epoch, o_done;
   size_t o_mono_eq, o_adj, o_resmask;
   size_t o_x, o_f, o_dx, o_r, o_out, o_out0, o_scratch, o_A, o_A0b, o_Rm, o_Vm, o_Y, o_Z, o_W, o_xn0, o_tau, o_rinv, o_salpha, o_v0, o_fabs, o_dxabs,
-      o_resabs, o_hist, o_rnorm;
+      o_resabs, o_hist, o_rnorm, o_t0;
 };
 
 struct mdn_ctx {
@@ -206,7 +206,8 @@ struct mdn_ctx {
   const double* cst = nullptr;
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;  // the QR of A0 overlaps the evaluation on this stream
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side2 = nullptr;  // W = Z Y of the pipelined QR, off its critical loop
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_w = nullptr;
   char* ws = nullptr;
   Layout L;
   std::string err;
@@ -406,8 +407,9 @@ static void compute_layout(mdn_ctx* ctx) {
   L.o_A0b = take(8 * KC * n * n * 2);  // A_0 of this step and of the next (pipelined QR)
   L.o_Rm = take(8 * (size_t)qr_xf_words(ctx->K) * ctx->C * n * n);  // extended floats
   L.o_Vm = take(8 * (size_t)qr_xf_words(ctx->K) * ctx->C * n * n);
-  L.o_Y = take(8 * KC * n * n);
-  L.o_Z = take(8 * KC * n * n);
+  L.o_Y = take(8 * KC * n * n * 2);  // Q^H and R^{-1} of this step and of the next
+  L.o_Z = take(8 * KC * n * n * 2);
+  L.o_t0 = take(8 * KC * n);
   L.o_W = take(8 * KC * n * n * 2);    // A_0^{-1} of this step and of the next
   L.o_xn0 = take(8 * KC * n);          // constant coefficients of the next series
   L.o_tau = take(8 * (size_t)qr_xf_words(ctx->K) * n);  // extended floats
@@ -460,8 +462,10 @@ mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degre
   // queue balance the load
   ctx->ed_grid = sms;
   if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_w, cudaEventDisableTiming) != cudaSuccess) {
     delete ctx;
     return MDN_ECUDA;
   }
@@ -661,12 +665,10 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
   return MDN_OK;
 }
 
-// Householder QR of A0 (the j = 0 slice of A) and W = A0^{-1} on stream st.
-static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* W, cudaStream_t st) {
+// Parameters of the QR of A0 into the Y/Z buffer pair `buf` with W out.
+static QrParams qr_params(mdn_ctx* ctx, const double* A0, long long NA0, double* W, int buf) {
   const Layout& L = ctx->L;
-  const long long n = ctx->n;
-  bump_kernel<<<1, 1, 0, st>>>(ctx->at<unsigned>(L.o_epoch));
-  CU(cudaGetLastError());
+  const long long n = ctx->n, KC = (long long)ctx->K * ctx->C;
   QrParams q{};
   q.n = ctx->n;
   q.nAc = (ctx->n + 3) / 4;
@@ -677,8 +679,8 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* 
   q.Nnn = n * n;
   q.Rm = ctx->at<uint64_t>(L.o_Rm);
   q.Vm = ctx->at<uint64_t>(L.o_Vm);
-  q.Y = ctx->at<double>(L.o_Y);
-  q.Z = ctx->at<double>(L.o_Z);
+  q.Y = ctx->at<double>(L.o_Y) + buf * KC * n * n;
+  q.Z = ctx->at<double>(L.o_Z) + buf * KC * n * n;
   q.W = W;
   q.tau = ctx->at<uint64_t>(L.o_tau);
   q.rinv = ctx->at<uint64_t>(L.o_rinv);
@@ -691,7 +693,24 @@ static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* 
   q.large = ctx->large_qr ? 1 : 0;
   q.Aw = q.Rm;  // the large variant's working columns take the place of R and the reflectors
   q.Yw = q.Vm;
+  return q;
+}
+
+// Householder QR of A0 (the j = 0 slice of A) and, unless skip_w, W = A0^{-1}
+// on stream st.  With skip_w the factors Z = R^{-1} and Y = Q^H are left in
+// buffer `buf` and run_qr_w forms W from them.
+static mdn_status run_qr(mdn_ctx* ctx, const double* A0, long long NA0, double* W, cudaStream_t st, int buf = 0,
+                         bool skip_w = false) {
+  bump_kernel<<<1, 1, 0, st>>>(ctx->at<unsigned>(ctx->L.o_epoch));
+  CU(cudaGetLastError());
+  QrParams q = qr_params(ctx, A0, NA0, W, buf);
+  q.skip_w = skip_w ? 1 : 0;
   CU(ctx->kt->qr(q, st));
+  return MDN_OK;
+}
+static mdn_status run_qr_w(mdn_ctx* ctx, double* W, int buf, cudaStream_t st) {
+  QrParams q = qr_params(ctx, nullptr, 0, W, buf);
+  CU(ctx->kt->qr_w(q, st));
   return MDN_OK;
 }
 
@@ -708,9 +727,12 @@ static int qr_launches(const mdn_ctx* ctx) { return 3 + (ctx->large_qr ? ctx->n 
 // (dx_0 = W r_0, and x_0 + dx_0 into the xnext0 buffer when x is given), the
 // event e0 recorded after it when not null, then the remaining stages on
 // `blocks` SMs.
+// With factors >= 0, stage 0 is formed from Z = R^{-1} and Y = Q^H of that
+// buffer (dx_0 = Z (Y r_0)) and the later stages wait for the event w_ready
+// (W formed on another stream) before they start.
 static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, long long NA0, const double* W,
                               const double* rhs, int sgn, double* dx, const double* x, cudaEvent_t e0, int blocks,
-                              bool transposed = false, int nst = 0) {
+                              bool transposed = false, int nst = 0, int factors = -1, cudaEvent_t w_ready = nullptr) {
   const Layout& L = ctx->L;
   const long long D = ctx->D, n = ctx->n;
   ph_begin(ctx, MDN_PHASE_FORWARD);
@@ -745,13 +767,20 @@ static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, l
   u.xdone = u.rdone + ctx->D;
   u.status = ctx->at<int>(L.o_status);
   u.spin_limit = ctx->wait_limit_ns;
+  if (factors >= 0) {
+    const long long off = (long long)factors * ctx->K * ctx->C * n * n;
+    u.Zs = ctx->at<double>(L.o_Z) + off;
+    u.Ys = ctx->at<double>(L.o_Y) + off;
+    u.t0 = ctx->at<double>(L.o_t0);
+  }
   CU(cudaMemsetAsync(u.rdone, 0, 4 * 2 * (size_t)ctx->D, ctx->stream));
   CU(ctx->kt->stage0(u, ctx->stream));
   if (e0) CU(cudaEventRecord(e0, ctx->stream));
+  if (w_ready) CU(cudaStreamWaitEvent(ctx->stream, w_ready, 0));
   // stages 1..nst-1 and the residuals of all stages (with one stage, the
   // residual of stage 0 alone)
   CU(ctx->kt->fsub(u, ctx->stream));
-  ph_end(ctx, MDN_PHASE_FORWARD, 3);
+  ph_end(ctx, MDN_PHASE_FORWARD, factors >= 0 ? 3 : 2);
   return MDN_OK;
 }
 
@@ -792,8 +821,21 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
   const int qb = qr_blocks(ctx);
   const bool overlap = ctx->side && qb <= (ctx->num_sms * 3) / 8;
   const int rest = overlap ? ctx->num_sms - qb : ctx->num_sms;
+  // W = Z Y on a third stream: the next step's stage 0 takes dx_0 from the
+  // factors, so the loop of QRs (stage 0 -> A_0 -> QR -> stage 0) does not
+  // wait for W; only the later stages of the forward substitution do
+  const bool split_w = overlap && !ctx->large_qr && ctx->side2;
   mdn_status r;
   *converged = false;
+  auto launch_w = [&](int buf) -> mdn_status {
+    CU(cudaStreamWaitEvent(ctx->side2, ctx->ev_join, 0));
+    ph_begin(ctx, MDN_PHASE_QR, ctx->side2);
+    mdn_status rr = run_qr_w(ctx, Wb[buf], buf, ctx->side2);
+    if (rr != MDN_OK) return rr;
+    ph_end(ctx, MDN_PHASE_QR, 1, ctx->side2);
+    CU(cudaEventRecord(ctx->ev_w, ctx->side2));
+    return MDN_OK;
+  };
   // A_0 and QR of the first step
   if (overlap) {
     CU(cudaEventRecord(ctx->ev_fork, ctx->stream));
@@ -802,9 +844,10 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
   cudaStream_t qs = overlap ? ctx->side : ctx->stream;
   ph_begin(ctx, MDN_PHASE_QR, qs);
   if ((r = run_a0(ctx, x, n * D, ctx->D, A0b[0], nn, qs)) != MDN_OK) return r;
-  if ((r = run_qr(ctx, A0b[0], nn, Wb[0], qs)) != MDN_OK) return r;
-  ph_end(ctx, MDN_PHASE_QR, qr_launches(ctx), qs);
+  if ((r = run_qr(ctx, A0b[0], nn, Wb[0], qs, 0, split_w)) != MDN_OK) return r;
+  ph_end(ctx, MDN_PHASE_QR, qr_launches(ctx) - (split_w ? 1 : 0), qs);
   if (overlap) CU(cudaEventRecord(ctx->ev_join, ctx->side));
+  if (split_w && (r = launch_w(0)) != MDN_OK) return r;
   if (ctx->stagger_first > 0) {
     // inactive coefficients contribute nothing to the norms of the step
     CU(cudaMemsetAsync(ctx->at<double>(L.o_fabs), 0, 8 * (size_t)n * D, ctx->stream));
@@ -819,16 +862,18 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
     const bool next = s + 1 < steps && qr_at(ctx, s + 1);
     // with no QR to run beside it the forward substitution takes every SM
     if ((r = run_forward(ctx, A, A0b[b], nn, Wb[b], f, -1, dx, x, (overlap && next) ? ctx->ev_fork : nullptr,
-                         (overlap && next) ? rest : ctx->num_sms, false, len)) != MDN_OK)
+                         (overlap && next) ? rest : ctx->num_sms, false, len, split_w ? b : -1,
+                         split_w ? ctx->ev_w : nullptr)) != MDN_OK)
       return r;
     if (next) {
       // A_0 and QR of step s+1 from x_0 + dx_0
       if (overlap) CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
       ph_begin(ctx, MDN_PHASE_QR, qs);
       if ((r = run_a0(ctx, ctx->at<double>(L.o_xn0), n, 1, A0b[b ^ 1], nn, qs)) != MDN_OK) return r;
-      if ((r = run_qr(ctx, A0b[b ^ 1], nn, Wb[b ^ 1], qs)) != MDN_OK) return r;
-      ph_end(ctx, MDN_PHASE_QR, qr_launches(ctx), qs);
+      if ((r = run_qr(ctx, A0b[b ^ 1], nn, Wb[b ^ 1], qs, b ^ 1, split_w)) != MDN_OK) return r;
+      ph_end(ctx, MDN_PHASE_QR, qr_launches(ctx) - (split_w ? 1 : 0), qs);
       if (overlap) CU(cudaEventRecord(ctx->ev_join, ctx->side));
+      if (split_w && (r = launch_w(b ^ 1)) != MDN_OK) return r;
     }
     UpdParams u{};
     u.n = ctx->n;
@@ -866,6 +911,7 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
   }
   // the QR of a step that is not run must be finished before returning
   if (overlap) CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+  if (split_w) CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_w, 0));
   return MDN_OK;
 }
 
@@ -1167,7 +1213,9 @@ void mdn_destroy(mdn_ctx* ctx) {
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_w) cudaEventDestroy(ctx->ev_w);
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->side2) cudaStreamDestroy(ctx->side2);
   delete ctx;
 }
 

@@ -573,7 +573,7 @@ int batch_occupancy(int threads) {
 template <int K, int C>
 const KernelTable* make_table() {
   static const KernelTable t = {K, C, &launch_ed<K, C>, &launch_a0<K, C>, &ed_blocks_per_sm<K, C>, &launch_assemble<K, C>,
-                                &launch_qr<K, C>, &launch_fsub<K, C>, &launch_stage0<K, C>,
+                                &launch_qr<K, C>, &launch_qr_w<K, C>, &launch_fsub<K, C>, &launch_stage0<K, C>,
                                 &launch_update<K, C>, &launch_adjoint<K, C>, &launch_fabry<K, C>,
                                 &launch_batch<K, C>, &batch_occupancy<K, C>, &launch_residual<K, C>,
                                 &launch_scale<K, C>};

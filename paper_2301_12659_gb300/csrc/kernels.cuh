@@ -1610,6 +1610,66 @@ __global__ void stage0_kernel(FsubParams p) {
   warp_count(&p.xdone[0]);
 }
 
+// Stage 0 from the factors, before W = Z Y exists (Newton's pipeline: the
+// next step's A_0 and QR then wait for Q^H and R^{-1} only): t = Y (sgn b_0)
+// one warp per row, then dx_0 = Z t, Z upper triangular.
+template <int K, int C>
+__global__ void stage0y_kernel(FsubParams p) {
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n = p.n, D = p.D;
+  if (i >= n) return;
+  CAcc<K, C> acc;
+  cacc_zero(acc);
+  for (int l = lane; l < n; l += 32) {
+    cmd<K, C> y, b;
+    ld(p.Ys, p.Nnn, (long long)i * n + l, y);
+    ld(p.rhs, p.Nx, (long long)l * D, b);
+    cacc_fma(acc, y, b);
+  }
+  cmd<K, C> s;
+  warp_sum_acc(acc, s);
+  if (lane == 0) {
+    cmd<K, C> b;
+    ld(p.rhs, p.Nx, (long long)i * D, b);
+    if (p.rhs_sign < 0) {
+      md_neg(s.re, s.re);
+      md_neg(s.im, s.im);
+      md_neg(b.re, b.re);
+      md_neg(b.im, b.im);
+    }
+    st(p.r, p.Nx, (long long)i * D, b);
+    st(p.t0, n, i, s);
+  }
+}
+template <int K, int C>
+__global__ void stage0z_kernel(FsubParams p) {
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n = p.n, D = p.D;
+  if (i >= n) return;
+  CAcc<K, C> acc;
+  cacc_zero(acc);
+  for (int l = i + lane; l < n; l += 32) {
+    cmd<K, C> z, t;
+    ld(p.Zs, p.Nnn, (long long)i * n + l, z);
+    ld(p.t0, n, l, t);
+    cacc_fma(acc, z, t);
+  }
+  cmd<K, C> s;
+  warp_sum_acc(acc, s);
+  if (lane == 0) {
+    st(p.dx, p.Nx, (long long)i * D, s);
+    if (p.xnext0) {
+      cmd<K, C> x0, xn;
+      ld(p.x, p.Nx, (long long)i * D, x0);
+      cmd_add(x0, s, xn);
+      st(p.xnext0, n, i, xn);
+    }
+  }
+  warp_count(&p.xdone[0]);
+}
+
 // x += dx; per-entry magnitudes of f and dx for the norms of the step.
 template <int K, int C>
 __global__ void update_kernel(UpdParams p) {
@@ -1929,7 +1989,12 @@ cudaError_t launch_qr(const QrParams& p, cudaStream_t s) {
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)qr_kernel<K, C>, dim3(p.nAc + p.nAi + p.nAz),
                                               dim3(QR_THREADS), args, smem, s);
   if (e != cudaSuccess) return e;
-  w_kernel<K, C><<<grid_for((long long)p.n * p.n * 32, 128), 128, 0, s>>>(q);
+  if (!p.skip_w) w_kernel<K, C><<<grid_for((long long)p.n * p.n * 32, 128), 128, 0, s>>>(q);
+  return cudaGetLastError();
+}
+template <int K, int C>
+cudaError_t launch_qr_w(const QrParams& p, cudaStream_t s) {
+  w_kernel<K, C><<<grid_for((long long)p.n * p.n * 32, 128), 128, 0, s>>>(p);
   return cudaGetLastError();
 }
 template <int K, int C>
@@ -1950,6 +2015,11 @@ cudaError_t launch_fsub(const FsubParams& p, cudaStream_t s) {
 }
 template <int K, int C>
 cudaError_t launch_stage0(const FsubParams& p, cudaStream_t s) {
+  if (p.Zs) {
+    stage0y_kernel<K, C><<<(p.n + 3) / 4, 128, 0, s>>>(p);
+    stage0z_kernel<K, C><<<(p.n + 3) / 4, 128, 0, s>>>(p);
+    return cudaGetLastError();
+  }
   stage0_kernel<K, C><<<(p.n + 3) / 4, 128, 0, s>>>(p);
   return cudaGetLastError();
 }

@@ -106,6 +106,7 @@ struct QrParams {
   const unsigned* epoch;
   int* status;
   long long spin_limit;  // nanoseconds a flag wait may last
+  int skip_w;  // 1: the launcher leaves W = Z Y to the w launcher (Newton's pipeline)
   // column-by-column variant for large n (no waits): the columns of A0 and
   // of the identity under the reflectors, as extended floats, column-major
   // ([W+1][C][n columns][n rows], element (i, c) at c*n + i)
@@ -133,6 +134,9 @@ struct FsubParams {
   long long Nnn;
   const double* rhs;
   double* r;     // accumulators, then r_k[i]   [K][C][n][D]
+  const double* Zs;  // stage 0 from the factors: dx_0 = Z (Y r_0) when not null
+  const double* Ys;  //   (Z = R^{-1}, Y = Q^H, before W = Z Y is formed)
+  double* t0;        //   Y r_0 [K][C][n]
   const double* x;   // stage0_kernel: current series, x_0 + dx_0 goes to xnext0
   double* xnext0;    // [K][C][n]
   double* dx;
@@ -278,6 +282,7 @@ struct KernelTable {
   int (*ed_blocks_per_sm)();
   cudaError_t (*assemble)(const AsmParams&, bool want_A, cudaStream_t);
   cudaError_t (*qr)(const QrParams&, cudaStream_t);  // QR, Q^H, R^{-1}, then W = R^{-1} Q^H
+  cudaError_t (*qr_w)(const QrParams&, cudaStream_t);  // W = Z Y alone
   cudaError_t (*fsub)(const FsubParams&, cudaStream_t);
   cudaError_t (*stage0)(const FsubParams&, cudaStream_t);
   cudaError_t (*update)(const UpdParams&, cudaStream_t);

@@ -201,6 +201,8 @@ struct mdn_ctx {
   int res_rows = 0;          // rows of the sampled residual monitor (0: all)
   int stagger_first = 0;     // staggered orders: order-1 steps with a QR each (0: off)
   long long wait_limit_ns = SPIN_LIMIT;  // bound of every device wait
+  int fsub_per_sm = 1;             // owner blocks per SM of the forward substitution
+  bool qr_running_beside = false;  // a QR of A0 runs on the side stream meanwhile
   std::vector<int> gvals, gidx_of_len;  // lane-group counts of the product lengths 1..D
   const double* coeff = nullptr;
   const double* cst = nullptr;
@@ -744,7 +746,12 @@ static mdn_status run_forward(mdn_ctx* ctx, const double* A, const double* A0, l
   u.nW = std::min(ctx->n, 4 * FSUB_WBLOCKS);
   const int wb = (u.nW + 3) / 4;
   const int nst_eff = (nst > 0 && nst <= ctx->D) ? nst : ctx->D;
-  u.nOwn = (int)std::min<long long>(4LL * std::max(1, blocks - wb), (long long)ctx->n * nst_eff);
+  // owner blocks per SM: one beside a concurrent QR (whose chain wants its
+  // SMs alone); otherwise ctx->fsub_per_sm, so that more warps share each
+  // sub-partition and hide the latency of the integer-limb row products
+  const int per_sm = (ctx->qr_running_beside || ctx->fsub_per_sm < 1) ? 1 : ctx->fsub_per_sm;
+  u.smem = per_sm == 1 ? QR_SMEM_RESERVE : per_sm == 2 ? 100 * 1024 : 70 * 1024;
+  u.nOwn = (int)std::min<long long>(4LL * per_sm * std::max(1, blocks - wb), (long long)ctx->n * nst_eff);
   u.late_stage = transposed ? ctx->D : std::min(ctx->late_stage, ctx->D);
   u.transpose = transposed ? 1 : 0;
   u.reverse = transposed ? 1 : 0;
@@ -861,10 +868,12 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
     if (overlap) CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     const bool next = s + 1 < steps && qr_at(ctx, s + 1);
     // with no QR to run beside it the forward substitution takes every SM
-    if ((r = run_forward(ctx, A, A0b[b], nn, Wb[b], f, -1, dx, x, (overlap && next) ? ctx->ev_fork : nullptr,
-                         (overlap && next) ? rest : ctx->num_sms, false, len, split_w ? b : -1,
-                         split_w ? ctx->ev_w : nullptr)) != MDN_OK)
-      return r;
+    ctx->qr_running_beside = overlap && next;
+    r = run_forward(ctx, A, A0b[b], nn, Wb[b], f, -1, dx, x, (overlap && next) ? ctx->ev_fork : nullptr,
+                    (overlap && next) ? rest : ctx->num_sms, false, len, split_w ? b : -1,
+                    split_w ? ctx->ev_w : nullptr);
+    ctx->qr_running_beside = false;
+    if (r != MDN_OK) return r;
     if (next) {
       // A_0 and QR of step s+1 from x_0 + dx_0
       if (overlap) CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));

@@ -2008,10 +2008,10 @@ cudaError_t launch_fsub(const FsubParams& p, cudaStream_t s) {
   FsubParams q = p;
   void* args[] = {(void*)&q};
   const int blocks = (p.nW + 3) / 4 + (p.nOwn + 3) / 4;
-  // one block per SM (the shared memory reservation): solve warps alone on
-  // their sub-partitions
+  // the shared memory reservation sets the blocks per SM (one: every warp
+  // alone on its sub-partition)
   return cudaLaunchCooperativeKernel((const void*)fsub_kernel<K, C>, dim3(blocks), dim3(FSUB_THREADS), args,
-                                     QR_SMEM_RESERVE, s);
+                                     p.smem > 0 ? p.smem : QR_SMEM_RESERVE, s);
 }
 template <int K, int C>
 cudaError_t launch_stage0(const FsubParams& p, cudaStream_t s) {

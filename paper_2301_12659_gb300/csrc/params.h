@@ -123,6 +123,7 @@ struct FsubParams {
   int nOwn;     // owner warps of the r_k[i] accumulators
   int late_stage;  // stages k >= late_stage form their updates in K/2 limbs (D: never)
   int nst;         // stages solved (<= D; staggered orders)
+  int smem;        // shared memory each block reserves (sets the blocks per SM)
   const int* resmask;  // rows whose residual the monitor forms (null: all)
   int transpose;   // 1: use A_j^T and W^T (the adjoint's solve with J^T)
   int reverse;     // 1: stage k works on coefficient D-1-k (J^T is block upper triangular)

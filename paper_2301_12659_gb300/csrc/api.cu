@@ -201,7 +201,8 @@ struct mdn_ctx {
   int res_rows = 0;          // rows of the sampled residual monitor (0: all)
   int stagger_first = 0;     // staggered orders: order-1 steps with a QR each (0: off)
   long long wait_limit_ns = SPIN_LIMIT;  // bound of every device wait
-  int fsub_per_sm = 1;             // owner blocks per SM of the forward substitution
+  int fsub_per_sm = 2;             // owner blocks per SM of the forward substitution
+  int ed_per_sm = 1;               // evaluation blocks per SM
   bool qr_running_beside = false;  // a QR of A0 runs on the side stream meanwhile
   std::vector<int> gvals, gidx_of_len;  // lane-group counts of the product lengths 1..D
   const double* coeff = nullptr;
@@ -299,6 +300,22 @@ static mdn_status build_tables(mdn_ctx* ctx, int M, const int32_t* eq, const int
     S += ctx->mono_k[m] + 1;
   }
   ctx->S = S;
+  // Evaluation blocks per SM: two (more warps per sub-partition hide the
+  // latency of the integer-limb products) when the products spread over the
+  // warps of one block per SM come to well over the longest single chain
+  // (the 3k-3 products of the largest monomial, which the warps sharing its
+  // sub-partition would slow down); one otherwise.
+  {
+    long long total = 0, longest = 1;
+    for (int m = 0; m < M; ++m) {
+      const long long pr = ctx->mono_k[m] == 1 ? 1 : 3LL * ctx->mono_k[m] - 3;
+      total += pr;
+      longest = std::max(longest, pr);
+    }
+    const long long warps1 = 4LL * std::max(1, ctx->num_sms);
+    ctx->ed_per_sm = (2 * total > 3 * longest * warps1) ? 2 : 1;
+    ctx->ed_grid = std::max(1, ctx->num_sms) * ctx->ed_per_sm;
+  }
   // work queue order: most expensive monomials first (longest processing time)
   ctx->order.resize(M);
   for (int m = 0; m < M; ++m) ctx->order[m] = m;
@@ -462,7 +479,7 @@ mdn_status mdn_create(mdn_ctx** out, int limbs, int is_complex, int n, int degre
   // one evaluation warp per SM sub-partition: four warps already fill an SM's
   // FP64 pipes, and fewer warps than monomials let the largest-first work
   // queue balance the load
-  ctx->ed_grid = sms;
+  ctx->ed_grid = sms * ctx->ed_per_sm;
   if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -621,7 +638,9 @@ static mdn_status run_evaluate(mdn_ctx* ctx, const double* x, double* f, double*
   e.G = G;
   e.kmax = ctx->kmax;
   e.Smax = ctx->Smax;
-  e.Wtot = std::min(blocks * (ED_THREADS / 32), ctx->Wtot);
+  const int per_sm = (ctx->qr_running_beside || ctx->ed_per_sm < 1) ? 1 : ctx->ed_per_sm;
+  e.smem = per_sm == 1 ? QR_SMEM_RESERVE : per_sm == 2 ? 100 * 1024 : 70 * 1024;
+  e.Wtot = std::min(blocks * per_sm * (ED_THREADS / 32), ctx->Wtot);
   e.x = x;
   e.Nx = n * D;
   e.coeff = ctx->coeff;
@@ -864,7 +883,10 @@ static mdn_status run_steps(mdn_ctx* ctx, int steps, double tol, int* done_out, 
   for (int s = 0; s < steps; ++s) {
     const int b = qr_at(ctx, s) ? (s & 1) : ((ctx->stagger_first - 1) & 1);
     const int len = stagger_len(ctx, s);
-    if ((r = run_evaluate(ctx, x, f, A, rest, len)) != MDN_OK) return r;
+    ctx->qr_running_beside = overlap;
+    r = run_evaluate(ctx, x, f, A, rest, len);
+    ctx->qr_running_beside = false;
+    if (r != MDN_OK) return r;
     if (overlap) CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     const bool next = s + 1 < steps && qr_at(ctx, s + 1);
     // with no QR to run beside it the forward substitution takes every SM
@@ -1041,7 +1063,10 @@ mdn_status mdn_adjoint(mdn_ctx* ctx, const double* x, const double* g, double* g
   ph_end(ctx, MDN_PHASE_QR, qr_launches(ctx), qs);
   if (overlap) CU(cudaEventRecord(ctx->ev_join, ctx->side));
   // A_1..A_d (the solve with J^T reads A_0 from the QR's copy)
-  if ((r = run_evaluate(ctx, x, f, A, overlap ? ctx->num_sms - qb : ctx->num_sms)) != MDN_OK) return r;
+  ctx->qr_running_beside = overlap;
+  r = run_evaluate(ctx, x, f, A, overlap ? ctx->num_sms - qb : ctx->num_sms);
+  ctx->qr_running_beside = false;
+  if (r != MDN_OK) return r;
   if (overlap) CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
   if ((r = run_forward(ctx, A, A0, n * n, W, g, +1, lam, nullptr, nullptr, ctx->num_sms, true)) != MDN_OK) return r;
   AdjParams a{};

@@ -1930,9 +1930,10 @@ cudaError_t launch_ed(const EdParams& p, int grid, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  // one block (four warps) per SM: exclusive FP64 pipes, also against the
-  // QR blocks that run at the same time on the other SMs
-  ed_kernel<K, C><<<grid, ED_THREADS, QR_SMEM_RESERVE, s>>>(p);
+  // the shared memory reservation sets the blocks per SM: one beside the QR
+  // blocks that run at the same time on the other SMs (no block shares
+  // their SMs), more otherwise
+  ed_kernel<K, C><<<grid, ED_THREADS, p.smem > 0 ? p.smem : QR_SMEM_RESERVE, s>>>(p);
   return cudaGetLastError();
 }
 template <int K, int C>

@@ -27,6 +27,7 @@ enum OpKind { OP_NONE = 0, OP_PRODUCT = 1, OP_COPY = 2 };
 struct EdParams {
   int n, D, M, P, G, kmax, Smax, Wtot;
   int len;  // coefficients computed (<= D, the stride); P and G are those of len
+  int smem;  // shared memory each block reserves (sets the blocks per SM)
   const double* x;
   long long Nx;  // n*D
   const double* coeff;

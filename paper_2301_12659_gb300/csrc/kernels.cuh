@@ -1090,7 +1090,7 @@ __device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, uint64_t* za, ui
 }
 
 template <int K, int C>
-__global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrParams p) {
+__global__ void __launch_bounds__(QR_THREADS, 1) qr_kernel(QrParams p) {
   extern __shared__ __align__(16) unsigned char qr_smem[];
   uint64_t* sm = reinterpret_cast<uint64_t*>(qr_smem);
   const int warp = threadIdx.x >> 5;

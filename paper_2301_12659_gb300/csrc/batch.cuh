@@ -359,6 +359,86 @@ __device__ bool batch_qr(const BWork& w, int n, int* sflag) {
 // ---------------------------------------------------------------------------
 // 3. forward substitution
 // ---------------------------------------------------------------------------
+// One thread's share of a dot product, sum over t < count of sgn a_t x_t
+// (pair(t, a, x) loads the t-th pair), in one fixed-point accumulator per
+// part at the thread's own scale (a first pass over the leading limbs'
+// exponents), rounded to K limbs once (xf.cuh); plain md accumulation for
+// K = 1.  With extra != null, -extra is added (once) as well.
+template <int K, int C, class Pair>
+__device__ __forceinline__ void thread_dot(int count, int first, int step, double sgn, Pair pair,
+                                           const cmd<K, C>* extra, cmd<K, C>& out) {
+  if constexpr (K >= 2) {
+    constexpr int W = xfn::xf_words_t<K>::value;
+    int er = 4 * xfn::XF_ZERO_E, ei = er, terms = 0;
+    for (int t = first; t < count; t += step) {
+      cmd<K, C> a, x;
+      pair(t, a, x);
+      const int ar = lead_exp(a.re[0]), xr = lead_exp(x.re[0]);
+      const int ai = C == 2 ? lead_exp(a.im[0]) : 2 * xfn::XF_ZERO_E;
+      const int xi = C == 2 ? lead_exp(x.im[0]) : 2 * xfn::XF_ZERO_E;
+      dot_exp<false, W, C>(ar, ai, xr, xi, er, ei);
+      ++terms;
+    }
+    if (extra) {
+      er = max(er, lead_exp(extra->re[0]));
+      if constexpr (C == 2) ei = max(ei, lead_exp(extra->im[0]));
+    }
+    const int head = acc_extra_head(C * terms + 1);
+    xfn::xfacc<W> acr, aci;
+    xfn::xfacc_init(acr, er + 1 + head);
+    if constexpr (C == 2) xfn::xfacc_init(aci, ei + 1 + head);
+    for (int t = first; t < count; t += step) {
+      cmd<K, C> a, x;
+      pair(t, a, x);
+      cxf<W, C> ax, xx;
+      xfn::xf_from_md<K, W>(a.re, ax.re);
+      xfn::xf_from_md<K, W>(x.re, xx.re);
+      if constexpr (C == 2) {
+        xfn::xf_from_md<K, W>(a.im, ax.im);
+        xfn::xf_from_md<K, W>(x.im, xx.im);
+      } else {
+        xfn::xf_zero(ax.im);
+        xfn::xf_zero(xx.im);
+      }
+      if (sgn < 0) cxf_neg(ax);
+      dot_fma<false>(acr, aci, ax, xx);
+    }
+    if (extra) {
+      xfn::xf<W> one, e;
+      xfn::xf_from_double(1.0, one);
+      xfn::xf_from_md<K, W>(extra->re, e);
+      xfn::xfacc_fma(acr, e, one, true);
+      if constexpr (C == 2) {
+        xfn::xf_from_md<K, W>(extra->im, e);
+        xfn::xfacc_fma(aci, e, one, true);
+      }
+    }
+    xfn::xf<W> r;
+    xfn::xfacc_get(acr, r);
+    xfn::xf_to_md<K, W>(r, out.re);
+    if constexpr (C == 2) {
+      xfn::xfacc_get(aci, r);
+      xfn::xf_to_md<K, W>(r, out.im);
+    } else {
+      md_zero(out.im);
+    }
+  } else {
+    CAcc<K, C> acc;
+    cacc_zero(acc);
+    for (int t = first; t < count; t += step) {
+      cmd<K, C> a, x;
+      pair(t, a, x);
+      if (sgn < 0) {
+        md_neg(a.re, a.re);
+        md_neg(a.im, a.im);
+      }
+      cacc_fma(acc, a, x);
+    }
+    if (extra) cacc_add(acc, *extra, -1.0);
+    cacc_get(acc, out);
+  }
+}
+
 // Thread tid < n*pp works on row i = tid / pp with share part = tid % pp of
 // the terms; partial sums meet in w.part and the first thread of the row
 // adds them up.
@@ -374,25 +454,15 @@ __device__ void batch_forward(const BWork& w, int n, int D) {
   for (int k = 0; k < D; ++k) {
     // r_k[i] = -f_k[i] - sum_{j=1..k} (A_j dx_{k-j})[i]
     if (rowt) {
-      CAcc<K, C> acc;
-      cacc_zero(acc);
-      const int terms = k * n;
-      for (int e = part; e < terms; e += pp) {
-        const int j = 1 + e / n, l = e - (j - 1) * n;
-        cmd<K, C> a, x;
-        ld(w.A, w.NA, (long long)j * nn + (long long)i * n + l, a);
-        ld(w.dx, w.Nf, (long long)l * D + (k - j), x);
-        md_neg(a.re, a.re);
-        md_neg(a.im, a.im);
-        cacc_fma(acc, a, x);
-      }
-      if (part == 0) {
-        cmd<K, C> fv;
-        ld(w.f, w.Nf, (long long)i * D + k, fv);
-        cacc_add(acc, fv, -1.0);
-      }
-      cmd<K, C> v;
-      cacc_get(acc, v);
+      cmd<K, C> fv, v;
+      if (part == 0) ld(w.f, w.Nf, (long long)i * D + k, fv);
+      thread_dot<K, C>(k * n, part, pp, -1.0,
+                       [&](int e, cmd<K, C>& a, cmd<K, C>& x) {
+                         const int j = 1 + e / n, l = e - (j - 1) * n;
+                         ld(w.A, w.NA, (long long)j * nn + (long long)i * n + l, a);
+                         ld(w.dx, w.Nf, (long long)l * D + (k - j), x);
+                       },
+                       part == 0 ? &fv : nullptr, v);
       st(w.part, w.NT, tid, v);
     }
     __syncthreads();
@@ -411,16 +481,13 @@ __device__ void batch_forward(const BWork& w, int n, int D) {
     __syncthreads();
     // dx_k[i] = (W r_k)[i]
     if (rowt) {
-      CAcc<K, C> acc;
-      cacc_zero(acc);
-      for (int l = part; l < n; l += pp) {
-        cmd<K, C> a, x;
-        ld(w.Y, w.Nnn, (long long)i * n + l, a);
-        ld(w.r, w.Nn, l, x);
-        cacc_fma(acc, a, x);
-      }
       cmd<K, C> v;
-      cacc_get(acc, v);
+      thread_dot<K, C>(n, part, pp, 1.0,
+                       [&](int l, cmd<K, C>& a, cmd<K, C>& x) {
+                         ld(w.Y, w.Nnn, (long long)i * n + l, a);
+                         ld(w.r, w.Nn, l, x);
+                       },
+                       nullptr, v);
       st(w.part, w.NT, tid, v);
     }
     __syncthreads();

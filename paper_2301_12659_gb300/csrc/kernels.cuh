@@ -630,44 +630,46 @@ __device__ __forceinline__ void cxf_neg(cxf<W, C>& v) {
   xfn::xf_neg(v.re);
   xfn::xf_neg(v.im);
 }
-template <int W, int C>
+// O (xf.cuh): the basic operations inline (throughput code) or called out
+// of line (latency-bound chains on one warp)
+template <class O = xfn::xf_ops_inline, int W, int C>
 __device__ __forceinline__ void cxf_add(const cxf<W, C>& a, const cxf<W, C>& b, cxf<W, C>& r) {
-  xfn::xf_add(a.re, b.re, r.re);
-  if constexpr (C == 2) xfn::xf_add(a.im, b.im, r.im);
+  O::add(a.re, b.re, r.re);
+  if constexpr (C == 2) O::add(a.im, b.im, r.im);
   else xfn::xf_zero(r.im);
 }
 // r = a b (conj_a: conj(a) b)
-template <bool conj_a, int W, int C>
+template <bool conj_a, class O = xfn::xf_ops_inline, int W, int C>
 __device__ __forceinline__ void cxf_mul(const cxf<W, C>& a, const cxf<W, C>& b, cxf<W, C>& r) {
   using namespace xfn;
   if constexpr (C == 1) {
-    xf_mul(a.re, b.re, r.re);
+    O::mul(a.re, b.re, r.re);
     xf_zero(r.im);
   } else {
     xf<W> t1, t2, t3, t4;
-    xf_mul(a.re, b.re, t1);
-    xf_mul(a.im, b.im, t2);
-    xf_mul(a.re, b.im, t3);
-    xf_mul(a.im, b.re, t4);
+    O::mul(a.re, b.re, t1);
+    O::mul(a.im, b.im, t2);
+    O::mul(a.re, b.im, t3);
+    O::mul(a.im, b.re, t4);
     if constexpr (conj_a) {
-      xf_add(t1, t2, r.re);
-      xf_sub(t3, t4, r.im);
+      O::add(t1, t2, r.re);
+      O::sub(t3, t4, r.im);
     } else {
-      xf_sub(t1, t2, r.re);
-      xf_add(t3, t4, r.im);
+      O::sub(t1, t2, r.re);
+      O::add(t3, t4, r.im);
     }
   }
 }
-template <bool conj_a, int W, int C>
+template <bool conj_a, class O = xfn::xf_ops_inline, int W, int C>
 __device__ __forceinline__ void cxf_fma(cxf<W, C>& acc, const cxf<W, C>& a, const cxf<W, C>& b) {
   cxf<W, C> t;
-  cxf_mul<conj_a>(a, b, t);
-  cxf_add(acc, t, acc);
+  cxf_mul<conj_a, O>(a, b, t);
+  cxf_add<O>(acc, t, acc);
 }
-template <int W, int C>
+template <class O = xfn::xf_ops_inline, int W, int C>
 __device__ __forceinline__ void cxf_scale(const cxf<W, C>& a, const xfn::xf<W>& s, cxf<W, C>& r) {
-  xfn::xf_mul(a.re, s, r.re);
-  if constexpr (C == 2) xfn::xf_mul(a.im, s, r.im);
+  O::mul(a.re, s, r.re);
+  if constexpr (C == 2) O::mul(a.im, s, r.im);
   else xfn::xf_zero(r.im);
 }
 // extended floats as the QR stores them: [W+1][C][N] 64-bit words, the W
@@ -747,14 +749,14 @@ __device__ __forceinline__ void dot_exp(int xr, int xi, int yr, int yi, int& er,
   er = max(er, max(xr + yr, xi + yi));
   ei = max(ei, max(xr + yi, xi + yr));
 }
-template <bool conj_x, int W, int C>
+template <bool conj_x, class O = xfn::xf_ops_inline, int W, int C>
 __device__ __forceinline__ void dot_fma(xfn::xfacc<W>& ar, xfn::xfacc<W>& ai, const cxf<W, C>& x, const cxf<W, C>& y) {
-  xfn::xfacc_fma(ar, x.re, y.re);
+  O::acc_fma(ar, x.re, y.re);
   if constexpr (C == 2) {
     // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr);  x y = (xr yr - xi yi) + i (xr yi + xi yr)
-    xfn::xfacc_fma(ar, x.im, y.im, !conj_x);
-    xfn::xfacc_fma(ai, x.re, y.im);
-    xfn::xfacc_fma(ai, x.im, y.re, conj_x);
+    O::acc_fma(ar, x.im, y.im, !conj_x);
+    O::acc_fma(ai, x.re, y.im);
+    O::acc_fma(ai, x.im, y.re, conj_x);
   }
 }
 template <int W, int C>
@@ -768,6 +770,12 @@ __device__ __forceinline__ void dot_finish(xfn::xfacc<W>& ar, xfn::xfacc<W>& ai,
     xfn::xf_zero(r.im);
   }
 }
+
+// The dataflow QR's warps and the pivot of the large-n QR are chains of
+// dependent operations on one warp, each run once per column: they call the
+// basic operations out of line (xf.cuh), so that their code stays in the
+// instruction cache.
+using QO = xfn::xf_ops_call;
 
 // dot = sum of conj(x_j[i]) y[i] over rows i = j..n-1 (x_j from Vm).
 template <int K, int C>
@@ -791,7 +799,7 @@ __device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const uin
     cxf<W, C> x, yi;
     xld<W, C>(p.Vm, p.Nnn, (long long)i * n + j, x);
     xld<W, C>(y, n, i, yi);
-    dot_fma<true>(ar, ai, x, yi);
+    dot_fma<true, QO>(ar, ai, x, yi);
   }
   dot_finish(ar, ai, dot);
 }
@@ -812,8 +820,8 @@ __device__ __forceinline__ void qr_norm2(const uint64_t* y, int n, int i0, xfn::
   for (int i = i0 + lane; i < n; i += 32) {
     cxf<W, C> v;
     xld<W, C>(y, n, i, v);
-    xfn::xfacc_fma(ar, v.re, v.re);
-    if constexpr (C == 2) xfn::xfacc_fma(ar, v.im, v.im);
+    QO::acc_fma(ar, v.re, v.re);
+    if constexpr (C == 2) QO::acc_fma(ar, v.im, v.im);
   }
   xfacc_warp_sum(ar);
   xfn::xfacc_get(ar, nrm);
@@ -829,7 +837,7 @@ __device__ __forceinline__ void qr_form_w(const QrParams& p, int j, const uint64
   xld<W, C>(p.salpha, p.n, j, sa);
   xld<W, C>(y, p.n, j, yj);
   w = dot;
-  cxf_fma<true>(w, sa, yj);
+  cxf_fma<true, QO>(w, sa, yj);
 }
 
 // y -= tau_j w v_j over rows j..n-1 (needs the ref flag of reflector j).
@@ -845,7 +853,7 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
   cxf<W, 1> tau;
   xld<W, 1>(p.tau, p.n, j, tau);
   cxf<W, C> ng;
-  cxf_scale(w, tau.re, ng);
+  cxf_scale<QO>(w, tau.re, ng);
   cxf_neg(ng);
   __syncwarp();
   // two rows per pass (i and i + 32): two independent chains to interleave
@@ -859,8 +867,8 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
     const int r2 = two ? i2 : i;
     xld<W, C>(p.Vm, p.Nnn, (long long)r2 * n + j, v2);
     xld<W, C>(y, n, r2, y2);
-    cxf_fma<false>(yi, ng, v);
-    cxf_fma<false>(y2, ng, v2);
+    cxf_fma<false, QO>(yi, ng, v);
+    cxf_fma<false, QO>(y2, ng, v2);
     xst<W, C>(y, n, i, yi);
     if (two) xst<W, C>(y, n, i2, y2);
     if (pub >= 0) {
@@ -906,8 +914,8 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
     if (lane == 0) xcopy<W, C>(y, n, j, p.Rm, p.Nnn, (long long)j * n + c);  // R[j][c] is final
     cxf<W, C> xv, q;
     xld<W, C>(y, n, j, xv);
-    cxf_mul<true>(xv, xv, q);
-    xf_sub(xN, q.re, xN);
+    cxf_mul<true, QO>(xv, xv, q);
+    QO::sub(xN, q.re, xN);
   }
   // publish x_c (rows c..n-1; the last update stored them for c > 0)
   if (c == 0)
@@ -933,38 +941,39 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
     xax0.s = 0;
   } else {
     xf<W> t1, t2, a2x, rx;
-    xf_mul(x0.re, x0.re, t1);
-    xf_mul(x0.im, x0.im, t2);
-    xf_add(t1, t2, a2x);
+    QO::mul(x0.re, x0.re, t1);
+    QO::mul(x0.im, x0.im, t2);
+    QO::add(t1, t2, a2x);
     const bool z = xf_is_zero(a2x);
     if (z) xf_from_double(1.0, a2x);
-    xf_rsqrt(a2x, rx);
-    xf_mul(a2x, rx, xax0);
-    xf_mul(x0.re, rx, sgr);
-    xf_mul(x0.im, rx, sgi);
+    xf_rsqrt<QO>(a2x, rx);
+    QO::mul(a2x, rx, xax0);
+    QO::mul(x0.re, rx, sgr);
+    QO::mul(x0.im, rx, sgi);
     if (z) {
       xf_zero(xax0);
       xf_from_double(1.0, sgr);
       xf_zero(sgi);
     }
   }
-  xf_rsqrt(xN, xry);
-  xf_mul(xN, xry, xal);
+  xf_rsqrt<QO>(xN, xry);
+  QO::mul(xN, xry, xal);
   xf<W> sre, sim;  // s|x_c|
   if constexpr (C == 1) {
     sre = xal;
     if (neg) xf_neg(sre);
     xf_zero(sim);
   } else {
-    xf_mul(sgr, xal, sre);
-    xf_mul(sgi, xal, sim);
+    QO::mul(sgr, xal, sre);
+    QO::mul(sgi, xal, sim);
   }
   {
     cxf<W, C> sa, v0;
     sa.re = sre;
     sa.im = sim;
-    xf_add(x0.re, sre, v0.re);
-    xf_add(x0.im, sim, v0.im);
+    QO::add(x0.re, sre, v0.re);
+    if constexpr (C == 2) QO::add(x0.im, sim, v0.im);
+    else xf_zero(v0.im);
     if (lane == 0) {
       xst<W, C>(p.salpha, p.n, c, sa);
       xst<W, C>(p.v0, p.n, c, v0);
@@ -975,9 +984,9 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
     cxf<W, 1> tau;
     xf_zero(tau.im);
     xf<W> t1, t2;
-    xf_mul(xal, xax0, t1);
-    xf_add(xN, t1, t2);
-    xf_recip(t2, tau.re);
+    QO::mul(xal, xax0, t1);
+    QO::add(xN, t1, t2);
+    xf_recip<QO>(t2, tau.re);
     if (singular) {
       xf_zero(tau.re);
       if (lane == 0) atomicOr(p.status, MDN_DEV_SINGULAR);
@@ -1073,11 +1082,11 @@ __device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, uint64_t* za, ui
           cxf<W, C> zk, rk;
           xld<W, C>(z, n, k, zk);
           xld<W, C>(p.Rm, p.Nnn, (long long)k * n + c, rk);
-          dot_fma<false>(ar, ai, zk, rk);
+          dot_fma<false, QO>(ar, ai, zk, rk);
         }
         cxf<W, C> sum;
         dot_finish(ar, ai, sum);
-        cxf_mul<false>(sum, rc, zc);
+        cxf_mul<false, QO>(sum, rc, zc);
         cxf_neg(zc);
       }
       if (lane == 0) {
@@ -1166,8 +1175,8 @@ __device__ void qrg_pivot(const QrParams& p, int j) {
   for (int i = j + lane; i < n; i += 32) {
     cxf<W, C> v;
     xld<W, C>(p.Aw, nn, col + i, v);
-    xfacc_fma(acc, v.re, v.re);
-    if constexpr (C == 2) xfacc_fma(acc, v.im, v.im);
+    QO::acc_fma(acc, v.re, v.re);
+    if constexpr (C == 2) QO::acc_fma(acc, v.im, v.im);
   }
   xfacc_warp_sum(acc);
   xf<W> xN;
@@ -1177,8 +1186,8 @@ __device__ void qrg_pivot(const QrParams& p, int j) {
   // |x| = N / sqrt(N), s = x_jj / |x_jj| (1 if x_jj = 0), v_jj = x_jj + s|x|,
   // tau = 1 / (N + |x| |x_jj|), 1 / R_jj = -conj(s) / |x|
   xf<W> xry, xal, xax0;
-  xf_rsqrt(xN, xry);
-  xf_mul(xN, xry, xal);
+  xf_rsqrt<QO>(xN, xry);
+  QO::mul(xN, xry, xal);
   cxf<W, C> x0;
   xld<W, C>(p.Aw, nn, col + j, x0);
   xf<W> sre, sim, sgr, sgi;
@@ -1192,44 +1201,45 @@ __device__ void qrg_pivot(const QrParams& p, int j) {
     xf_zero(sim);
   } else {
     xf<W> t1, t2, a2x, rx;
-    xf_mul(x0.re, x0.re, t1);
-    xf_mul(x0.im, x0.im, t2);
-    xf_add(t1, t2, a2x);
+    QO::mul(x0.re, x0.re, t1);
+    QO::mul(x0.im, x0.im, t2);
+    QO::add(t1, t2, a2x);
     const bool z = xf_is_zero(a2x);
     if (z) xf_from_double(1.0, a2x);
-    xf_rsqrt(a2x, rx);
-    xf_mul(a2x, rx, xax0);
-    xf_mul(x0.re, rx, sgr);
-    xf_mul(x0.im, rx, sgi);
+    xf_rsqrt<QO>(a2x, rx);
+    QO::mul(a2x, rx, xax0);
+    QO::mul(x0.re, rx, sgr);
+    QO::mul(x0.im, rx, sgi);
     if (z) {
       xf_zero(xax0);
       xf_from_double(1.0, sgr);
       xf_zero(sgi);
     }
-    xf_mul(sgr, xal, sre);
-    xf_mul(sgi, xal, sim);
+    QO::mul(sgr, xal, sre);
+    QO::mul(sgi, xal, sim);
   }
   cxf<W, C> sa, v0, rinv;
   sa.re = sre;
   sa.im = sim;
-  xf_add(x0.re, sre, v0.re);
-  xf_add(x0.im, sim, v0.im);
+  QO::add(x0.re, sre, v0.re);
+  if constexpr (C == 2) QO::add(x0.im, sim, v0.im);
+  else xf_zero(v0.im);
   cxf<W, 1> tau;
   xf_zero(tau.im);
   {
     xf<W> t1, t2;
-    xf_mul(xal, xax0, t1);
-    xf_add(xN, t1, t2);
-    xf_recip(t2, tau.re);
+    QO::mul(xal, xax0, t1);
+    QO::add(xN, t1, t2);
+    xf_recip<QO>(t2, tau.re);
   }
   if constexpr (C == 1) {
     rinv.re = xry;
     if (!neg) xf_neg(rinv.re);
     xf_zero(rinv.im);
   } else {
-    xf_mul(sgr, xry, rinv.re);
+    QO::mul(sgr, xry, rinv.re);
     xf_neg(rinv.re);
-    xf_mul(sgi, xry, rinv.im);
+    QO::mul(sgi, xry, rinv.im);
   }
   if (singular) {
     xf_zero(tau.re);

@@ -610,6 +610,82 @@ XF_FN void xfacc_fma(xfacc<W>& a, const xf<W>& x, const xf<W>& y, bool neg = fal
   add_words<W + 2>(a.w, yv, mask & 1ULL);
 }
 
+// ---------------------------------------------------------------------------
+// inline or out-of-line calls of the basic operations
+// ---------------------------------------------------------------------------
+// Every inlined operation is a new copy of its code (a few hundred
+// instructions at W = 4).  Code that one warp runs once per value, such as
+// the pivot scalars of a Householder reflector, is then bound by
+// instruction fetch: its copies are not in the instruction cache the next
+// time they run.  Called out of line, one copy per width serves every call
+// site and stays cached.  Arguments and results go by value, in registers.
+// xf_ops_inline suits throughput code (independent operations interleave);
+// xf_ops_call suits latency-bound chains on one warp.
+#if defined(__CUDACC__)
+template <int W>
+__device__ __noinline__ xf<W> xf_mul_ol(const xf<W> a, const xf<W> b) {
+  xf<W> r;
+  xf_mul(a, b, r);
+  return r;
+}
+template <int W>
+__device__ __noinline__ xf<W> xf_add_ol(const xf<W> a, const xf<W> b) {
+  xf<W> r;
+  xf_add(a, b, r);
+  return r;
+}
+template <int W>
+__device__ __noinline__ xf<W> xf_sub_ol(const xf<W> a, const xf<W> b) {
+  xf<W> r;
+  xf_sub(a, b, r);
+  return r;
+}
+template <int W>
+__device__ __noinline__ xfacc<W> xfacc_fma_ol(xfacc<W> acc, const xf<W> x, const xf<W> y, const bool neg) {
+  xfacc_fma(acc, x, y, neg);
+  return acc;
+}
+#endif
+
+struct xf_ops_inline {
+  template <int W>
+  static XF_FN void mul(const xf<W>& a, const xf<W>& b, xf<W>& r) { xf_mul(a, b, r); }
+  template <int W>
+  static XF_FN void add(const xf<W>& a, const xf<W>& b, xf<W>& r) { xf_add(a, b, r); }
+  template <int W>
+  static XF_FN void sub(const xf<W>& a, const xf<W>& b, xf<W>& r) { xf_sub(a, b, r); }
+  template <int W>
+  static XF_FN void acc_fma(xfacc<W>& acc, const xf<W>& x, const xf<W>& y, bool neg = false) {
+    xfacc_fma(acc, x, y, neg);
+  }
+};
+
+struct xf_ops_call {
+#if defined(__CUDA_ARCH__)
+  template <int W>
+  static __device__ __forceinline__ void mul(const xf<W>& a, const xf<W>& b, xf<W>& r) { r = xf_mul_ol<W>(a, b); }
+  template <int W>
+  static __device__ __forceinline__ void add(const xf<W>& a, const xf<W>& b, xf<W>& r) { r = xf_add_ol<W>(a, b); }
+  template <int W>
+  static __device__ __forceinline__ void sub(const xf<W>& a, const xf<W>& b, xf<W>& r) { r = xf_sub_ol<W>(a, b); }
+  template <int W>
+  static __device__ __forceinline__ void acc_fma(xfacc<W>& acc, const xf<W>& x, const xf<W>& y, bool neg = false) {
+    acc = xfacc_fma_ol<W>(acc, x, y, neg);
+  }
+#else
+  template <int W>
+  static XF_FN void mul(const xf<W>& a, const xf<W>& b, xf<W>& r) { xf_mul(a, b, r); }
+  template <int W>
+  static XF_FN void add(const xf<W>& a, const xf<W>& b, xf<W>& r) { xf_add(a, b, r); }
+  template <int W>
+  static XF_FN void sub(const xf<W>& a, const xf<W>& b, xf<W>& r) { xf_sub(a, b, r); }
+  template <int W>
+  static XF_FN void acc_fma(xfacc<W>& acc, const xf<W>& x, const xf<W>& y, bool neg = false) {
+    xfacc_fma(acc, x, y, neg);
+  }
+#endif
+};
+
 template <int W>
 XF_FN void xfacc_get(const xfacc<W>& a, xf<W>& r) {
   const bool neg = (a.w[W + 1] >> 63) != 0ULL;
@@ -753,64 +829,64 @@ XF_FN void xf_resize(const xf<W1>& a, xf<W2>& r) {
 }
 
 // one Newton step for 1/a at width V: y += y (1 - a y)
-template <int V>
+template <int V, class O>
 XF_FN void recip_step(const xf<V>& a, xf<V>& y) {
   xf<V> one, t, u;
   xf_from_double(1.0, one);
-  xf_mul(a, y, t);
-  xf_sub(one, t, u);
-  xf_mul(y, u, t);
-  xf_add(y, t, u);
+  O::mul(a, y, t);
+  O::sub(one, t, u);
+  O::mul(y, u, t);
+  O::add(y, t, u);
   y = u;
 }
 // one Newton step for 1/sqrt(a) at width V: y += y (1 - a y^2) / 2
-template <int V>
+template <int V, class O>
 XF_FN void rsqrt_step(const xf<V>& a, xf<V>& y) {
   xf<V> one, t, u;
   xf_from_double(1.0, one);
-  xf_mul(a, y, t);
-  xf_mul(t, y, u);
-  xf_sub(one, u, t);
-  xf_mul(y, t, u);
+  O::mul(a, y, t);
+  O::mul(t, y, u);
+  O::sub(one, u, t);
+  O::mul(y, t, u);
   xf_mul_pow2(u, -1);
-  xf_add(y, u, t);
+  O::add(y, u, t);
   y = t;
 }
 // one third-order step for 1/sqrt(a) at width V: with e = 1 - a y^2,
 // y += y (e/2 + 3e^2/8), which cubes the relative error (to 5/16 of it)
-template <int V>
+template <int V, class O>
 XF_FN void rsqrt_step3(const xf<V>& a, xf<V>& y) {
   xf<V> one, t, u, e, c38, h;
   xf_from_double(1.0, one);
   xf_from_double(0.375, c38);
-  xf_mul(a, y, t);
-  xf_mul(t, y, u);
-  xf_sub(one, u, e);
-  xf_mul(e, c38, t);
+  O::mul(a, y, t);
+  O::mul(t, y, u);
+  O::sub(one, u, e);
+  O::mul(e, c38, t);
   xf_from_double(0.5, u);
-  xf_add(u, t, h);
-  xf_mul(e, h, t);
-  xf_mul(y, t, u);
-  xf_add(y, u, t);
+  O::add(u, t, h);
+  O::mul(e, h, t);
+  O::mul(y, t, u);
+  O::add(y, u, t);
   y = t;
 }
 // the third-order step at width V on the W-word a and y
-template <int V, int W>
+template <int V, class O, int W>
 XF_FN void rsqrt3_at(const xf<W>& a, xf<W>& y) {
   xf<V> av, yv;
   xf_resize<V>(a, av);
   xf_resize<V>(y, yv);
-  rsqrt_step3<V>(av, yv);
+  rsqrt_step3<V, O>(av, yv);
   xf_resize<W>(yv, y);
 }
 // the step at width V on the W-word a and y
-template <int V, bool RSQRT, int W>
+template <int V, bool RSQRT, class O, int W>
 XF_FN void newton_at(const xf<W>& a, xf<W>& y) {
   xf<V> av, yv;
   xf_resize<V>(a, av);
   xf_resize<V>(y, yv);
-  if constexpr (RSQRT) rsqrt_step<V>(av, yv);
-  else recip_step<V>(av, yv);
+  if constexpr (RSQRT) rsqrt_step<V, O>(av, yv);
+  else recip_step<V, O>(av, yv);
   xf_resize<W>(yv, y);
 }
 // From a 53-bit seed each step doubles the correct bits up to the width it
@@ -823,28 +899,28 @@ XF_FN void newton_at(const xf<W>& a, xf<W>& y) {
 // square root (a seed of about 52 bits)
 // starts with a third-order step at 2 words (-> 125 bits) and then doubles:
 // widths 2; 2, 4; 2, 4, 7 for W = 2, 4, 7 (64W bits).
-template <bool RSQRT, int W>
+template <bool RSQRT, class O, int W>
 XF_FN void newton_steps(const xf<W>& a, xf<W>& y) {
   if constexpr (RSQRT && W >= 2) {
-    rsqrt3_at<2>(a, y);
-    if constexpr (W >= 4) newton_at<4, true>(a, y);
-    if constexpr (W > 4) newton_at<W, true>(a, y);
+    rsqrt3_at<2, O>(a, y);
+    if constexpr (W >= 4) newton_at<4, true, O>(a, y);
+    if constexpr (W > 4) newton_at<W, true, O>(a, y);
     return;
   }
-  newton_at<1, RSQRT>(a, y);
-  if constexpr (W >= 2) newton_at<2, RSQRT>(a, y);
-  if constexpr (W >= 4) newton_at<4, RSQRT>(a, y);
-  if constexpr (W > 4) newton_at<W, RSQRT>(a, y);
+  newton_at<1, RSQRT, O>(a, y);
+  if constexpr (W >= 2) newton_at<2, RSQRT, O>(a, y);
+  if constexpr (W >= 4) newton_at<4, RSQRT, O>(a, y);
+  if constexpr (W > 4) newton_at<W, RSQRT, O>(a, y);
 }
 
-// r = 1 / a, a nonzero
-template <int W>
+// r = 1 / a, a nonzero (O: how the basic operations are called)
+template <class O = xf_ops_inline, int W>
 XF_FN void xf_recip(const xf<W>& a, xf<W>& r) {
   xf<W> y;
   xf_from_double(drecip(xf_mant_double(a)), y);
   y.e -= a.e;
   y.s = a.s;
-  newton_steps<false>(a, y);
+  newton_steps<false, O>(a, y);
   r = y;
 }
 
@@ -860,12 +936,12 @@ XF_FN void xf_rsqrt_seed(const xf<W>& a, xf<W>& y) {
   y.e -= eh;
 }
 
-// r = 1 / sqrt(a), a > 0
-template <int W>
+// r = 1 / sqrt(a), a > 0 (O: how the basic operations are called)
+template <class O = xf_ops_inline, int W>
 XF_FN void xf_rsqrt(const xf<W>& a, xf<W>& r) {
   xf<W> y;
   xf_rsqrt_seed(a, y);
-  newton_steps<true>(a, y);
+  newton_steps<true, O>(a, y);
   r = y;
 }
 

@@ -856,24 +856,22 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
   cxf_scale<QO>(w, tau.re, ng);
   cxf_neg(ng);
   __syncwarp();
-  // two rows per pass (i and i + 32): two independent chains to interleave
-  for (int i = j + lane; i < n; i += 64) {
-    const int i2 = i + 32;
-    const bool two = i2 < n;
-    cxf<W, C> v, yi, v2, y2;
-    if (i == j) xld<W, C>(p.v0, p.n, j, v);
-    else xld<W, C>(p.Vm, p.Nnn, (long long)i * n + j, v);
-    xld<W, C>(y, n, i, yi);
-    const int r2 = two ? i2 : i;
-    xld<W, C>(p.Vm, p.Nnn, (long long)r2 * n + j, v2);
-    xld<W, C>(y, n, r2, y2);
+  // passes of 32 rows with a trip count uniform over the warp, and the warp
+  // converged before the (out-of-line) arithmetic, so that each call runs
+  // once for all lanes; a lane past the last row recomputes row j unstored
+  for (int i0 = j; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    const bool row = i < n;
+    const int r = row ? i : j;
+    const bool diag = r == j;
+    cxf<W, C> v, yi;
+    xld<W, C>(diag ? p.v0 : p.Vm, diag ? (long long)p.n : p.Nnn, diag ? (long long)j : (long long)r * n + j, v);
+    xld<W, C>(y, n, r, yi);
+    __syncwarp();
     cxf_fma<false, QO>(yi, ng, v);
-    cxf_fma<false, QO>(y2, ng, v2);
-    xst<W, C>(y, n, i, yi);
-    if (two) xst<W, C>(y, n, i2, y2);
-    if (pub >= 0) {
-      if (i >= pub) xst<W, C>(p.Vm, p.Nnn, (long long)i * n + pub, yi);
-      if (two && i2 >= pub) xst<W, C>(p.Vm, p.Nnn, (long long)i2 * n + pub, y2);
+    if (row) {
+      xst<W, C>(y, n, i, yi);
+      if (pub >= 0 && i >= pub) xst<W, C>(p.Vm, p.Nnn, (long long)i * n + pub, yi);
     }
   }
   __syncwarp();
@@ -912,6 +910,7 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
     if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
     qr_update<K, C>(p, j, y, w, j == c - 1 ? c : -1);
     if (lane == 0) xcopy<W, C>(y, n, j, p.Rm, p.Nnn, (long long)j * n + c);  // R[j][c] is final
+    __syncwarp();
     cxf<W, C> xv, q;
     xld<W, C>(y, n, j, xv);
     cxf_mul<true, QO>(xv, xv, q);

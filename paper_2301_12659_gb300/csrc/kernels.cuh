@@ -777,9 +777,11 @@ __device__ __forceinline__ void dot_finish(xfn::xfacc<W>& ar, xfn::xfacc<W>& ai,
 // instruction cache.
 using QO = xfn::xf_ops_call;
 
-// dot = sum of conj(x_j[i]) y[i] over rows i = j..n-1 (x_j from Vm).
+// dot = sum of conj(x_j[i]) y[i] over rows i = j..n-1 (x_j from Vm); the
+// rows of x_j are also staged in the warp's shared buffer xs, where the
+// update by reflector j reads them (row j there becomes v_jj in qr_form_w).
 template <int K, int C>
-__device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const uint64_t* y,
+__device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const uint64_t* y, uint64_t* xs,
                                              cxf<xfn::xf_words_t<K>::value, C>& dot) {
   constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
@@ -799,6 +801,7 @@ __device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const uin
     cxf<W, C> x, yi;
     xld<W, C>(p.Vm, p.Nnn, (long long)i * n + j, x);
     xld<W, C>(y, n, i, yi);
+    xst<W, C>(xs, n, i, x);
     dot_fma<true, QO>(ar, ai, x, yi);
   }
   dot_finish(ar, ai, dot);
@@ -827,15 +830,18 @@ __device__ __forceinline__ void qr_norm2(const uint64_t* y, int n, int i0, xfn::
   xfn::xfacc_get(ar, nrm);
 }
 
-// w = dot + conj(s_j|x_j|) y[j] (needs the alpha flag of reflector j)
+// w = dot + conj(s_j|x_j|) y[j], and v_jj into row j of xs (needs the alpha
+// flag of reflector j)
 template <int K, int C>
-__device__ __forceinline__ void qr_form_w(const QrParams& p, int j, const uint64_t* y,
+__device__ __forceinline__ void qr_form_w(const QrParams& p, int j, const uint64_t* y, uint64_t* xs,
                                           const cxf<xfn::xf_words_t<K>::value, C>& dot,
                                           cxf<xfn::xf_words_t<K>::value, C>& w) {
   constexpr int W = xfn::xf_words_t<K>::value;
   cxf<W, C> sa, yj;
   xld<W, C>(p.salpha, p.n, j, sa);
   xld<W, C>(y, p.n, j, yj);
+  if ((threadIdx.x & 31) == 0) xcopy<W, C>(p.v0, p.n, j, xs, p.n, j);
+  __syncwarp();
   w = dot;
   cxf_fma<true, QO>(w, sa, yj);
 }
@@ -845,7 +851,7 @@ template <int K, int C>
 // With pub >= 0 (the column warp's last reflector, j = pub - 1), rows
 // pub..n-1 of the result, the column x_pub that its owner publishes next,
 // are also stored to Vm as they are formed.
-__device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
+__device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y, const uint64_t* xs,
                                           const cxf<xfn::xf_words_t<K>::value, C>& w, int pub = -1) {
   constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
@@ -863,9 +869,8 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
     const int i = i0 + lane;
     const bool row = i < n;
     const int r = row ? i : j;
-    const bool diag = r == j;
     cxf<W, C> v, yi;
-    xld<W, C>(diag ? p.v0 : p.Vm, diag ? (long long)p.n : p.Nnn, diag ? (long long)j : (long long)r * n + j, v);
+    xld<W, C>(xs, n, r, v);  // v_j: x_j below the diagonal, v_jj on it
     xld<W, C>(y, n, r, yi);
     __syncwarp();
     cxf_fma<false, QO>(yi, ng, v);
@@ -880,9 +885,11 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
 // Column warp c: its column under the reflectors 0..c-1, then reflector c.
 // Reflector j is applied in three parts: the dot product x_j^H y as soon as
 // x_j is out (col[j]), w = dot + conj(s_j|x_j|) y[j] as soon as s_j|x_j| and
-// v_jj are out (alpha[j]), and y -= tau_j w v_j once tau_j is out (ref[j]).
+// v_jj are out (alpha[j]), and y -= tau_j w v_j once tau_j is out (ref[j]).  The entries
+// R_jc, final as the updates go, are copied out after the pivot (off the
+// chain from one column's tau to the next's).
 template <int K, int C>
-__device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
+__device__ void qr_column(const QrParams& p, int c, uint64_t* y, uint64_t* xs, unsigned ep) {
   using namespace xfn;
   constexpr int W = xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
@@ -904,13 +911,11 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
   for (int j = 0; j < c; ++j) {
     if (!warp_wait(&fcol[j], ep, p.spin_limit, p.status)) return;
     cxf<W, C> dot, w;
-    qr_lookahead<K, C>(p, j, y, dot);
+    qr_lookahead<K, C>(p, j, y, xs, dot);
     if (!warp_wait(&fal[j], ep, p.spin_limit, p.status)) return;
-    qr_form_w<K, C>(p, j, y, dot, w);
+    qr_form_w<K, C>(p, j, y, xs, dot, w);
     if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
-    qr_update<K, C>(p, j, y, w, j == c - 1 ? c : -1);
-    if (lane == 0) xcopy<W, C>(y, n, j, p.Rm, p.Nnn, (long long)j * n + c);  // R[j][c] is final
-    __syncwarp();
+    qr_update<K, C>(p, j, y, xs, w, j == c - 1 ? c : -1);
     cxf<W, C> xv, q;
     xld<W, C>(y, n, j, xv);
     cxf_mul<true, QO>(xv, xv, q);
@@ -1013,12 +1018,13 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, unsigned ep) {
   }
   if (singular) cxf_zero(rinv);
   if (lane == 0) xst<W, C>(p.rinv, p.n, c, rinv);
+  for (int i = lane; i < c; i += 32) xcopy<W, C>(y, n, i, p.Rm, p.Nnn, (long long)i * n + c);  // R_ic, i < c
   warp_publish(&frinv[c], ep);
 }
 
 // Identity warp e: Q^H e_e as the reflectors appear (column e of Y = Q^H).
 template <int K, int C>
-__device__ void qr_identity(const QrParams& p, int e, uint64_t* y, unsigned ep) {
+__device__ void qr_identity(const QrParams& p, int e, uint64_t* y, uint64_t* xs, unsigned ep) {
   constexpr int W = xfn::xf_words_t<K>::value;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
@@ -1033,9 +1039,9 @@ __device__ void qr_identity(const QrParams& p, int e, uint64_t* y, unsigned ep) 
   for (int j = 0; j < n; ++j) {
     if (!warp_wait(&fref[j], ep, p.spin_limit, p.status)) return;
     cxf<W, C> dot, w;
-    qr_lookahead<K, C>(p, j, y, dot);
-    qr_form_w<K, C>(p, j, y, dot, w);
-    qr_update<K, C>(p, j, y, w);
+    qr_lookahead<K, C>(p, j, y, xs, dot);
+    qr_form_w<K, C>(p, j, y, xs, dot, w);
+    qr_update<K, C>(p, j, y, xs, w);
   }
   for (int i = lane; i < n; i += 32) {
     cxf<W, C> v;
@@ -1109,11 +1115,11 @@ __global__ void __launch_bounds__(QR_THREADS, 1) qr_kernel(QrParams p) {
   if (b < p.nAc) {
     const int c = b * (QR_THREADS / 32) + warp;
     if (c >= n) return;
-    qr_column<K, C>(p, c, sm + warp * col, ep);
+    qr_column<K, C>(p, c, sm + warp * col, sm + (QR_THREADS / 32 + warp) * col, ep);
   } else if (b < p.nAc + p.nAi) {
     const int e = (b - p.nAc) * (QR_THREADS / 32) + warp;
     if (e >= n) return;
-    qr_identity<K, C>(p, e, sm + warp * col, ep);
+    qr_identity<K, C>(p, e, sm + warp * col, sm + (QR_THREADS / 32 + warp) * col, ep);
   } else {
     const int g = (b - p.nAc - p.nAi) * (QR_THREADS / 32) + warp;
     if (g > (n - 1) / 2) return;

@@ -648,6 +648,7 @@ __device__ __noinline__ xfacc<W> xfacc_fma_ol(xfacc<W> acc, const xf<W> x, const
 #endif
 
 struct xf_ops_inline {
+  static constexpr bool call = false;
   template <int W>
   static XF_FN void mul(const xf<W>& a, const xf<W>& b, xf<W>& r) { xf_mul(a, b, r); }
   template <int W>
@@ -661,6 +662,7 @@ struct xf_ops_inline {
 };
 
 struct xf_ops_call {
+  static constexpr bool call = true;
 #if defined(__CUDA_ARCH__)
   template <int W>
   static __device__ __forceinline__ void mul(const xf<W>& a, const xf<W>& b, xf<W>& r) { r = xf_mul_ol<W>(a, b); }
@@ -828,121 +830,253 @@ XF_FN void xf_resize(const xf<W1>& a, xf<W2>& r) {
   r.s = a.s;
 }
 
-// one Newton step for 1/a at width V: y += y (1 - a y)
-template <int V, class O>
-XF_FN void recip_step(const xf<V>& a, xf<V>& y) {
-  xf<V> one, t, u;
-  xf_from_double(1.0, one);
-  O::mul(a, y, t);
-  O::sub(one, t, u);
-  O::mul(y, u, t);
-  O::add(y, t, u);
-  y = u;
+// ---------------------------------------------------------------------------
+// reciprocal and reciprocal square root: Newton's iteration in fixed point
+// ---------------------------------------------------------------------------
+// Columns LO .. NA+NB-1 of the product of the NA-word a and the NB-word b
+// (column k weighs 2^(64k)) into out[0 .. NA+NB-1-LO].  Below column LO only
+// the products of column LO-1 enter (their high halves, and the carry of
+// their low halves), so out[0] may fall short of the exact column by fewer
+// than NA + NB units.
+template <int NA, int NB, int LO>
+XF_FN void mul_top(const uint64_t (&a)[NA], const uint64_t (&b)[NB], uint64_t (&out)[NA + NB - LO]) {
+  uint64_t carry = 0;
+#pragma unroll
+  for (int k = LO - 1; k <= NA + NB - 1; ++k) {
+    uint64_t s = carry, c = 0;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const int j = k - i;
+      if (j >= 0 && j < NB) add_count(s, c, a[i] * b[j]);
+      const int jh = k - 1 - i;
+      if (k > LO - 1 && jh >= 0 && jh < NB) add_count(s, c, umulhi(a[i], b[jh]));
+    }
+    if (k >= LO) out[k - LO] = s;
+    carry = c;
+  }
 }
-// one Newton step for 1/sqrt(a) at width V: y += y (1 - a y^2) / 2
-template <int V, class O>
-XF_FN void rsqrt_step(const xf<V>& a, xf<V>& y) {
-  xf<V> one, t, u;
-  xf_from_double(1.0, one);
-  O::mul(a, y, t);
-  O::mul(t, y, u);
-  O::sub(one, u, t);
-  O::mul(y, t, u);
-  xf_mul_pow2(u, -1);
-  O::add(y, u, t);
-  y = t;
+
+// Y += sgn C over N words, sgn = -1 when neg (two's complement, no
+// branch).  A sum that reaches 2^(64N) (y = 1 - ulp, the leading words of m
+// exactly 1, so that the iteration heads for 1 itself) stays at 2^(64N) - 1.
+template <int N>
+XF_FN void add_signed(uint64_t (&Y)[N], const uint64_t (&C)[N], bool neg) {
+  const uint64_t mask = neg ? ~0ULL : 0ULL;
+  uint64_t t[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) t[i] = C[i] ^ mask;
+  const uint64_t cy = add_words<N>(Y, t, mask & 1ULL);
+  const uint64_t sat = (!neg && cy != 0ULL) ? ~0ULL : 0ULL;
+#pragma unroll
+  for (int i = 0; i < N; ++i) Y[i] |= sat;
 }
-// one third-order step for 1/sqrt(a) at width V: with e = 1 - a y^2,
-// y += y (e/2 + 3e^2/8), which cubes the relative error (to 5/16 of it)
-template <int V, class O>
-XF_FN void rsqrt_step3(const xf<V>& a, xf<V>& y) {
-  xf<V> one, t, u, e, c38, h;
-  xf_from_double(1.0, one);
-  xf_from_double(0.375, c38);
-  O::mul(a, y, t);
-  O::mul(t, y, u);
-  O::sub(one, u, e);
-  O::mul(e, c38, t);
-  xf_from_double(0.5, u);
-  O::add(u, t, h);
-  O::mul(e, h, t);
-  O::mul(y, t, u);
-  O::add(y, u, t);
-  y = t;
+
+// D = 2^(64V+63+sh) - P over V+1 words (two's complement), then |D| in
+// place; returns whether D < 0.  sh = 0 or -1.
+template <int V>
+XF_FN bool newton_residual(const uint64_t (&P)[V + 1], int sh, uint64_t (&D)[V + 1]) {
+  uint64_t one[V + 1];
+#pragma unroll
+  for (int i = 0; i <= V; ++i) {
+    D[i] = ~P[i];
+    one[i] = 0ULL;
+  }
+  one[V] = sh == 0 ? (1ULL << 63) : (1ULL << 62);
+  add_words<V + 1>(D, one, 1ULL);  // 2^(...) + ~P + 1 = 2^(...) - P
+  const bool neg = (D[V] >> 63) != 0ULL;
+  const uint64_t mask = neg ? ~0ULL : 0ULL;
+  uint64_t z[V + 1];
+#pragma unroll
+  for (int i = 0; i <= V; ++i) {
+    D[i] ^= mask;
+    z[i] = 0ULL;
+  }
+  add_words<V + 1>(D, z, mask & 1ULL);
+  return neg;
 }
-// the third-order step at width V on the W-word a and y
-template <int V, class O, int W>
-XF_FN void rsqrt3_at(const xf<W>& a, xf<W>& y) {
-  xf<V> av, yv;
-  xf_resize<V>(a, av);
-  xf_resize<V>(y, yv);
-  rsqrt_step3<V, O>(av, yv);
-  xf_resize<W>(yv, y);
+
+// One Newton step for y = 1/m at width V:  m = A / 2^(64V-1) in [1, 2) (A:
+// the leading V words of the mantissa), y = Y / 2^(64V) in (1/2, 1);
+//   D = 1 - m y (a signed fixed-point number, small),  y += y D.
+// With k correct bits in y, |D| < 2^(1-k) and the step leaves about 2k
+// (up to the 64V of the width): the products are formed to the words
+// that the result keeps.
+template <int V>
+XF_FN void recip_fx_step(const uint64_t (&A)[V], uint64_t (&Y)[V]) {
+  uint64_t P[V + 1], D[V + 1], U[V + 1], C[V];
+  mul_top<V, V, V - 1>(A, Y, P);  // m y = P / 2^(64V+63)
+  const bool neg = newton_residual<V>(P, 0, D);
+  mul_top<V, V + 1, V>(Y, D, U);  // y |D| = (U / 2^63) / 2^(64V)
+#pragma unroll
+  for (int i = 0; i < V; ++i) C[i] = (U[i] >> 63) | (U[i + 1] << 1);
+  add_signed<V>(Y, C, neg);
 }
-// the step at width V on the W-word a and y
-template <int V, bool RSQRT, class O, int W>
-XF_FN void newton_at(const xf<W>& a, xf<W>& y) {
-  xf<V> av, yv;
-  xf_resize<V>(a, av);
-  xf_resize<V>(y, yv);
-  if constexpr (RSQRT) rsqrt_step<V, O>(av, yv);
-  else recip_step<V, O>(av, yv);
-  xf_resize<W>(yv, y);
+
+// One Newton step for y = 1/sqrt(m) at width V:  m = A / 2^(64V-1-odd) in
+// [1, 4), y = Y / 2^(64V) in (1/2, 1];  D = 1 - m y^2,  y += y D / 2.
+template <int V>
+XF_FN void rsqrt_fx_step(const uint64_t (&A)[V], bool odd, uint64_t (&Y)[V]) {
+  uint64_t Q[V], P[V + 1], D[V + 1], U[V + 1], C[V];
+  mul_top<V, V, V>(Y, Y, Q);  // y^2 = Q / 2^(64V)
+  mul_top<V, V, V - 1>(A, Q, P);  // m y^2 = P / 2^(64V+63-odd)
+  const bool neg = newton_residual<V>(P, odd ? -1 : 0, D);
+  mul_top<V, V + 1, V>(Y, D, U);
+  // y D / 2 = U / 2^(64V+64-odd) (as Y's fixed point)
+#pragma unroll
+  for (int i = 0; i < V; ++i) C[i] = odd ? ((U[i] >> 63) | (U[i + 1] << 1)) : U[i + 1];
+  add_signed<V>(Y, C, neg);
 }
-// From a 53-bit seed each step doubles the correct bits up to the width it
-// runs at, so the early steps run narrower.  The reciprocal, seeded with the
-// correctly rounded double reciprocal of the leading 53 bits (about 52
-// correct bits), runs one step at each width 1, 2, 4, ... up to W: about
-// 62, 122, 242, 440 bits after the steps at 1, 2, 4, 7 words (each step's
-// truncation costs a few bits below its width), at least 53K + 8 bits for
-// the K = 1, 2, 4, 8 limbs that W = 1, 2, 4, 7 serve.  The reciprocal
-// square root (a seed of about 52 bits)
-// starts with a third-order step at 2 words (-> 125 bits) and then doubles:
-// widths 2; 2, 4; 2, 4, 7 for W = 2, 4, 7 (64W bits).
-template <bool RSQRT, class O, int W>
-XF_FN void newton_steps(const xf<W>& a, xf<W>& y) {
-  if constexpr (RSQRT && W >= 2) {
-    rsqrt3_at<2, O>(a, y);
-    if constexpr (W >= 4) newton_at<4, true, O>(a, y);
-    if constexpr (W > 4) newton_at<W, true, O>(a, y);
+
+// The leading V words of the W-word mantissa, and Y from width V to V2.
+template <int V, int W>
+XF_FN void lead_words(const uint64_t (&m)[W], uint64_t (&A)[V]) {
+#pragma unroll
+  for (int i = 0; i < V; ++i) A[i] = m[W - V + i];
+}
+template <int V2, int V>
+XF_FN void widen(const uint64_t (&Y)[V], uint64_t (&Y2)[V2]) {
+#pragma unroll
+  for (int i = 0; i < V2; ++i) Y2[i] = i < V2 - V ? 0ULL : Y[i - (V2 - V)];
+}
+
+// the step at width V on the iterate Yp of width VP < V
+template <bool RSQRT, int V, int W, int VP>
+XF_FN void fx_step_at(const uint64_t (&m)[W], bool odd, const uint64_t (&Yp)[VP], uint64_t (&Y)[V]) {
+  uint64_t A[V];
+  widen<V>(Yp, Y);
+  lead_words<V>(m, A);
+  if constexpr (RSQRT) rsqrt_fx_step<V>(A, odd, Y);
+  else recip_fx_step<V>(A, Y);
+}
+
+// The steps at widths 1, 2, 4, ... up to W from a double seed y0 in (0, 1):
+// the seed has about 52 correct bits and each step doubles them, up to the
+// width it runs at (62, 122, 242, 440 bits after the steps at 1, 2, 4, 7
+// words; each step's truncations cost a few bits below its width), at least
+// 53K + 8 bits for the K = 1, 2, 4, 8 limbs that W = 1, 2, 4, 7 serve.  The
+// reciprocal square root's step leaves 3/2 of the squared error, so at
+// W = 4 it takes a step at 3 words before the last (122 -> 186 -> 256).
+template <bool RSQRT, int W>
+XF_FN void newton_fx(const uint64_t (&m)[W], bool odd, double y0, uint64_t (&Y)[W]) {
+  uint64_t Y1[1], A1[1];
+  Y1[0] = (uint64_t)(y0 * 18446744073709551616.0);  // y0 2^64 < 2^64, exact
+  lead_words<1>(m, A1);
+  if constexpr (RSQRT) rsqrt_fx_step<1>(A1, odd, Y1);
+  else recip_fx_step<1>(A1, Y1);
+  if constexpr (W == 1) {
+    Y[0] = Y1[0];
+    return;
+  } else {
+    uint64_t Y2[2];
+    fx_step_at<RSQRT, 2>(m, odd, Y1, Y2);
+    if constexpr (W == 2) {
+      Y[0] = Y2[0];
+      Y[1] = Y2[1];
+    } else if constexpr (W == 4 && RSQRT) {
+      uint64_t Y3[3];
+      fx_step_at<RSQRT, 3>(m, odd, Y2, Y3);
+      fx_step_at<RSQRT, 4>(m, odd, Y3, Y);
+    } else if constexpr (W == 4) {
+      fx_step_at<RSQRT, 4>(m, odd, Y2, Y);
+    } else {
+      uint64_t Y4[4];
+      fx_step_at<RSQRT, 4>(m, odd, Y2, Y4);
+      fx_step_at<RSQRT, W>(m, odd, Y4, Y);
+    }
+  }
+}
+
+// Y / 2^(64W) (y in (1/2, 1), or a few units below 1/2) as an xf value of
+// exponent e - 1: normalised by one bit where the top bit is clear.
+template <int W>
+XF_FN void fx_to_xf(const uint64_t (&Y)[W], int e, int s, xf<W>& r) {
+  const bool top = (Y[W - 1] >> 63) != 0ULL;
+#pragma unroll
+  for (int i = 0; i < W; ++i) r.m[i] = top ? Y[i] : ((Y[i] << 1) | (i > 0 ? Y[i - 1] >> 63 : 0ULL));
+  r.e = top ? e - 1 : e - 2;
+  r.s = s;
+}
+
+// whether the mantissa is exactly 2^(64W-1) (the value a power of two)
+template <int W>
+XF_FN bool mant_is_pow2(const xf<W>& a) {
+  bool p = a.m[W - 1] == (1ULL << 63);
+#pragma unroll
+  for (int i = 0; i < W - 1; ++i) p = p && a.m[i] == 0ULL;
+  return p;
+}
+
+// r = 1 / a, a nonzero:  1/a = (1/m) 2^(-e) for a = m 2^e, m in [1, 2).
+template <int W>
+XF_FN void xf_recip_fx(const xf<W>& a, xf<W>& r) {
+  if (mant_is_pow2(a)) {  // 1/m = 1 exactly
+    xf_from_double(1.0, r);
+    r.e = -a.e;
+    r.s = a.s;
     return;
   }
-  newton_at<1, RSQRT, O>(a, y);
-  if constexpr (W >= 2) newton_at<2, RSQRT, O>(a, y);
-  if constexpr (W >= 4) newton_at<4, RSQRT, O>(a, y);
-  if constexpr (W > 4) newton_at<W, RSQRT, O>(a, y);
+  double y0 = drecip(xf_mant_double(a));  // in (1/2, 1]; below 1 since m > 1
+  y0 = y0 < 1.0 ? y0 : 1.0 - 0x1p-53;
+  uint64_t Y[W];
+  newton_fx<false>(a.m, false, y0, Y);
+  fx_to_xf(Y, -a.e, a.s, r);
 }
 
-// r = 1 / a, a nonzero (O: how the basic operations are called)
+// r = 1 / sqrt(a), a > 0:  a = m' 2^e' with e' even and m' = m or 2m in
+// [1, 4), 1/sqrt(a) = (1/sqrt(m')) 2^(-e'/2).
+template <int W>
+XF_FN void xf_rsqrt_fx(const xf<W>& a, xf<W>& r) {
+  const bool odd = (a.e & 1) != 0;
+  const int eh = (odd ? a.e - 1 : a.e) / 2;
+  if (!odd && mant_is_pow2(a)) {  // m' = 1
+    xf_from_double(1.0, r);
+    r.e = -eh;
+    return;
+  }
+  const double md = xf_mant_double(a);
+  double y0 = drsqrt(odd ? 2.0 * md : md);
+  y0 = y0 < 1.0 ? y0 : 1.0 - 0x1p-53;
+  uint64_t Y[W];
+  newton_fx<true>(a.m, odd, y0, Y);
+  fx_to_xf(Y, -eh, 0, r);
+}
+
+#if defined(__CUDACC__)
+template <int W>
+__device__ __noinline__ xf<W> xf_recip_ol(const xf<W> a) {
+  xf<W> r;
+  xf_recip_fx(a, r);
+  return r;
+}
+template <int W>
+__device__ __noinline__ xf<W> xf_rsqrt_ol(const xf<W> a) {
+  xf<W> r;
+  xf_rsqrt_fx(a, r);
+  return r;
+}
+#endif
+
+// r = 1 / a, a nonzero, and r = 1 / sqrt(a), a > 0 (O: inline, or one
+// out-of-line call on the device)
 template <class O = xf_ops_inline, int W>
 XF_FN void xf_recip(const xf<W>& a, xf<W>& r) {
-  xf<W> y;
-  xf_from_double(drecip(xf_mant_double(a)), y);
-  y.e -= a.e;
-  y.s = a.s;
-  newton_steps<false, O>(a, y);
-  r = y;
+#if defined(__CUDA_ARCH__)
+  if constexpr (O::call) {
+    r = xf_recip_ol<W>(a);
+    return;
+  }
+#endif
+  xf_recip_fx(a, r);
 }
-
-// the double seed of 1 / sqrt(a), a > 0: a = M 2^e with M in [1, 2); for
-// odd e take 2M 2^(e-1)
-template <int W>
-XF_FN void xf_rsqrt_seed(const xf<W>& a, xf<W>& y) {
-  const bool odd = (a.e & 1) != 0;
-  double md = xf_mant_double(a);
-  md = odd ? md * 2.0 : md;
-  const int eh = (odd ? a.e - 1 : a.e) / 2;
-  xf_from_double(drsqrt(md), y);
-  y.e -= eh;
-}
-
-// r = 1 / sqrt(a), a > 0 (O: how the basic operations are called)
 template <class O = xf_ops_inline, int W>
 XF_FN void xf_rsqrt(const xf<W>& a, xf<W>& r) {
-  xf<W> y;
-  xf_rsqrt_seed(a, y);
-  newton_steps<true, O>(a, y);
-  r = y;
+#if defined(__CUDA_ARCH__)
+  if constexpr (O::call) {
+    r = xf_rsqrt_ol<W>(a);
+    return;
+  }
+#endif
+  xf_rsqrt_fx(a, r);
 }
 
 }  // namespace xfn

@@ -161,6 +161,31 @@ def test_reciprocal_and_rsqrt(lib, K):
 
 
 @pytest.mark.parametrize("K", [1, 2, 4, 8])
+def test_reciprocal_and_rsqrt_near_powers_of_two(lib, K):
+    """1/a and 1/sqrt(a) for a just above and below powers of two (1 + 2^-k,
+    2 - 2^-k, 4 (1 - 2^-k) and their multiples by 2^j): mantissas whose
+    leading words are exactly those of a power of two, where the iteration
+    heads for 1 (or 1/2) itself; same bounds as above."""
+    W = WORDS[K]
+    tol = Fr(2) ** (8 - 64 * W)
+    ks = [k for k in (1, 2, 30, 52, 53, 60, 63, 64, 65, 100, 127, 128, 129, 150, 200, 255, 256, 257, 300, 400)
+          if k <= 53 * K - 1]
+    for k in ks:
+        for base in (1 + Fr(1, 2 ** k), 2 - Fr(1, 2 ** k), 4 * (1 - Fr(1, 2 ** k)), 1 - Fr(1, 2 ** k)):
+            for j in (-7, 0, 3):
+                A = base * Fr(2) ** j
+                a = np.array(ex.fr_to_md(A, K))
+                if ex.md_to_fr(a) != A:
+                    continue
+                y = ex.md_to_fr(_op(lib, K, "recip", a, extra=True))
+                assert abs(y * A - 1) <= tol, (k, base, j)
+                assert abs(ex.md_to_fr(_op(lib, K, "recip", a)) * A - 1) <= Fr(2) ** (2 - 53 * K)
+                r = ex.md_to_fr(_op(lib, K, "rsqrt", a, extra=True))
+                assert abs(r * r * A - 1) <= tol, (k, base, j)
+                assert abs(ex.md_to_fr(_op(lib, K, "rsqrt", a)) ** 2 * A - 1) <= Fr(2) ** (3 - 53 * K)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
 @pytest.mark.parametrize("D", [1, 7, 32, 64])
 def test_fixed_point_convolution(lib, K, D):
     """c = a b mod t^D, one fixed-point accumulator per coefficient: error

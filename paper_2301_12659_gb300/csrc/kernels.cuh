@@ -577,7 +577,8 @@ __global__ void a0_assemble_kernel(A0Params p) {
 // x_j = column j (rows j..n-1) after H_0..H_{j-1}, s_j = x_jj / |x_jj| (+1 for
 // x_jj = 0), tau_j = 1 / (|x_j| (|x_j| + |x_jj|)); then H_j x_j = -s_j |x_j| e_j.
 // Three flags per column (values = the launch epoch):
-//   col[j]  x_j is published (rows j..n-1 of Vm column j);
+//   col[j]  x_j is published (rows j..n-1 of Vm column j, stored column
+//           after column so that a warp reads a column in whole lines);
 //   ref[j]  the scalars s_j|x_j|, v_jj and tau_j are published;
 //   rinv[j] 1 / R_jj is published.
 // Look-ahead: the warp of column c forms x_j^H y_c as soon as col[j]
@@ -787,21 +788,25 @@ __device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const uin
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   int er = 2 * xfn::XF_ZERO_E, ei = er;
+  // one pass over global memory: x_j into xs (its exponents on the way)
+#pragma unroll 2
   for (int i = j + lane; i < n; i += 32) {
-    int xr, xi, yr, yi;
-    xld_exp<W, C>(p.Vm, p.Nnn, (long long)i * n + j, xr, xi);
+    cxf<W, C> x;
+    int yr, yi;
+    xld<W, C>(p.Vm, p.Nnn, (long long)j * n + i, x);
+    xst<W, C>(xs, n, i, x);
     xld_exp<W, C>(y, n, i, yr, yi);
-    dot_exp<true, W, C>(xr, xi, yr, yi, er, ei);
+    dot_exp<true, W, C>(x.re.e, C == 2 ? x.im.e : 2 * xfn::XF_ZERO_E, yr, yi, er, ei);
   }
+  __syncwarp();
   xfn::xfacc<W> ar, ai;
   const int head = acc_extra_head(C * (n - j));
   xfn::xfacc_init(ar, warp_max(er) + head);
   if constexpr (C == 2) xfn::xfacc_init(ai, warp_max(ei) + head);
   for (int i = j + lane; i < n; i += 32) {
     cxf<W, C> x, yi;
-    xld<W, C>(p.Vm, p.Nnn, (long long)i * n + j, x);
+    xld<W, C>(xs, n, i, x);
     xld<W, C>(y, n, i, yi);
-    xst<W, C>(xs, n, i, x);
     dot_fma<true, QO>(ar, ai, x, yi);
   }
   dot_finish(ar, ai, dot);
@@ -876,7 +881,7 @@ __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y,
     cxf_fma<false, QO>(yi, ng, v);
     if (row) {
       xst<W, C>(y, n, i, yi);
-      if (pub >= 0 && i >= pub) xst<W, C>(p.Vm, p.Nnn, (long long)i * n + pub, yi);
+      if (pub >= 0 && i >= pub) xst<W, C>(p.Vm, p.Nnn, (long long)pub * n + i, yi);
     }
   }
   __syncwarp();
@@ -923,7 +928,7 @@ __device__ void qr_column(const QrParams& p, int c, uint64_t* y, uint64_t* xs, u
   }
   // publish x_c (rows c..n-1; the last update stored them for c > 0)
   if (c == 0)
-    for (int i = c + lane; i < n; i += 32) xcopy<W, C>(y, n, i, p.Vm, p.Nnn, (long long)i * n + c);
+    for (int i = c + lane; i < n; i += 32) xcopy<W, C>(y, n, i, p.Vm, p.Nnn, (long long)c * n + i);
   warp_publish(&fcol[c], ep);
   // N = |x_c|^2 by downdating, recomputed when it is not positive or more
   // than 8 bits cancelled

@@ -94,7 +94,7 @@ struct QrParams {
   long long NA;   // stride of the A array the A0 slice lives in
   long long Nnn;  // n*n
   uint64_t* Rm;  // R and the reflectors x_j, as extended floats [W+1][C][n][n]
-  uint64_t* Vm;  // (W mantissa words and a word of exponent and sign)
+  uint64_t* Vm;  // (W mantissa words and a word of exponent and sign); Vm column-major
   double* Y;  // Q^H (identity columns under all reflectors)
   double* Z;  // R^{-1}
   double* W;

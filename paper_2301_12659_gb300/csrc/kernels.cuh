@@ -1399,10 +1399,12 @@ __global__ void w_kernel(QrParams p) {
 // in xdone[k].  Owners also form the residual r_k - A_0 dx_k of their rows.
 // Counters are zeroed before the launch; every wait is bounded.
 // ---------------------------------------------------------------------------
+// One count for the warp: the warp barrier orders every lane's earlier
+// stores before lane 0's release add (cumulative, as in warp_publish), so a
+// reader that acquires the count sees them.
 __device__ __forceinline__ void warp_count(unsigned* c) {
-  __threadfence();
   __syncwarp();
-  if ((threadIdx.x & 31) == 0) atomicAdd(c, 1u);
+  if ((threadIdx.x & 31) == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c) : "memory");
   __syncwarp();
 }
 __device__ __forceinline__ bool warp_wait_count(const unsigned* c, unsigned target, long long limit_ns, int* status) {

@@ -1418,6 +1418,16 @@ __device__ __forceinline__ void ld_acc(const double* p, long long N, long long i
   acc_set(a.re, v.re);
   if constexpr (C == 2) acc_set(a.im, v.im);
 }
+template <int K, int C>
+__device__ __forceinline__ void st_acc(double* p, long long N, long long i, const CAcc<K, C>& a) {
+  cmd<K, C> v;
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    v.re[l] = a.re.l[l];
+    v.im[l] = (C == 2) ? a.im.l[l] : 0.0;
+  }
+  st(p, N, i, v);
+}
 
 // sum_l M[row_off + l*ms] x_l over the warp (a row of a row-major n-by-n
 // block for ms = 1, a column for ms = n) with x_l = coefficient kx of
@@ -1471,55 +1481,6 @@ __device__ __forceinline__ void warp_rowdot(const double* Mp, long long NM, long
     }
     warp_sum_acc(acc, out);
   }
-}
-
-// r0 - sum_l M[row_off + l*ms] x_l (K >= 2): the products and -r0 in one
-// fixed-point accumulator (r0 entered once, by lane 0) at the scale of the
-// larger of the two, rounded to K limbs once; all lanes get it.  The
-// subtraction stays on the integer pipe: no md additions in FP64.
-template <int K, int C>
-__device__ __forceinline__ void warp_rowdot_from(const double* Mp, long long NM, long long row_off, int ms,
-                                                 const double* xp, long long Nx, int n, int D, int kx,
-                                                 const cmd<K, C>& r0, cmd<K, C>& out) {
-  static_assert(K >= 2, "K = 1 keeps the md accumulation");
-  constexpr int W = xfn::xf_words_t<K>::value;
-  const int lane = threadIdx.x & 31;
-  int er = lead_exp(r0.re[0]);
-  int ei = C == 2 ? lead_exp(r0.im[0]) : 2 * xfn::XF_ZERO_E;
-  for (int l = lane; l < n; l += 32) {
-    const long long ia = row_off + (long long)l * ms, ix = (long long)l * D + kx;
-    const int ar = lead_exp(Mp[ia]), xr = lead_exp(xp[ix]);
-    const int ai = C == 2 ? lead_exp(Mp[NM + ia]) : 2 * xfn::XF_ZERO_E;
-    const int xi = C == 2 ? lead_exp(xp[Nx + ix]) : 2 * xfn::XF_ZERO_E;
-    dot_exp<false, W, C>(ar, ai, xr, xi, er, ei);
-  }
-  xfn::xfacc<W> acr, aci;
-  const int head = acc_extra_head(C * n + 1);
-  xfn::xfacc_init(acr, warp_max(er) + 1 + head);
-  if constexpr (C == 2) xfn::xfacc_init(aci, warp_max(ei) + 1 + head);
-  // acc = sum M x - r0; the result is -acc
-  if (lane == 0) {
-    xfn::xf<W> one, rx;
-    xfn::xf_from_double(1.0, one);
-    xfn::xf_from_md<K, W>(r0.re, rx);
-    xfn::xfacc_fma(acr, rx, one, true);
-    if constexpr (C == 2) {
-      xfn::xf_from_md<K, W>(r0.im, rx);
-      xfn::xfacc_fma(aci, rx, one, true);
-    }
-  }
-  for (int l = lane; l < n; l += 32) {
-    cxf<W, C> a, x;
-    cxf_load<K, W, C>(Mp, NM, row_off + (long long)l * ms, a);
-    cxf_load<K, W, C>(xp, Nx, (long long)l * D + kx, x);
-    dot_fma<false>(acr, aci, a, x);
-  }
-  cxf<W, C> sum;
-  dot_finish(acr, aci, sum);
-  cxf_neg(sum);
-  xfn::xf_to_md<K, W>(sum.re, out.re);
-  if constexpr (C == 2) xfn::xf_to_md<K, W>(sum.im, out.im);
-  else md_zero(out.im);
 }
 
 template <int K, int C>
@@ -1581,20 +1542,9 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
       const int k = (int)(q / n), i = (int)(q - (long long)k * n);
       if (k <= m) continue;
       // r_k[i] -= (A_{k-m} dx_m)[i]
-      const long long ir = (long long)i * D + co(k);
-      cmd<K, C> rk;
-      bool fused = false;
+      cmd<K, C> ax;
       if constexpr (K >= 2) {
-        if (k < p.late_stage) {
-          cmd<K, C> r0;
-          ld(p.r, p.Nx, ir, r0);
-          warp_rowdot_from<K, C>(p.A, p.NA, row((long long)(k - m) * nn, i), ms, p.dx, p.Nx, n, D, co(m), r0, rk);
-          fused = true;
-        }
-      }
-      if (!fused) {
-        cmd<K, C> ax;
-        if constexpr (K >= 2) {
+        if (k >= p.late_stage) {
           // the leading K/2 doubles of A and dx are K/2-limb values (limb
           // index outermost in the layout): the same pointers and strides
           cmd<K / 2, C> h;
@@ -1608,29 +1558,32 @@ __global__ void __launch_bounds__(FSUB_THREADS) fsub_kernel(FsubParams p) {
         } else {
           warp_rowdot<K, C>(p.A, p.NA, row((long long)(k - m) * nn, i), ms, p.dx, p.Nx, n, D, co(m), ax);
         }
-        CAcc<K, C> a;
-        ld_acc(p.r, p.Nx, ir, a);
-        cacc_add(a, ax, -1.0);
-        cacc_get(a, rk);
+      } else {
+        warp_rowdot<K, C>(p.A, p.NA, row((long long)(k - m) * nn, i), ms, p.dx, p.Nx, n, D, co(m), ax);
       }
-      if (lane == 0) st(p.r, p.Nx, ir, rk);
-      __syncwarp();
-      if (k == m + 1) warp_count(&p.rdone[k]);
+      CAcc<K, C> a;
+      ld_acc(p.r, p.Nx, (long long)i * D + co(k), a);
+      cacc_add(a, ax, -1.0);
+      if (k == m + 1) {
+        cmd<K, C> r;
+        cacc_get(a, r);
+        if (lane == 0) st(p.r, p.Nx, (long long)i * D + co(k), r);
+        __syncwarp();
+        warp_count(&p.rdone[k]);
+      } else {
+        if (lane == 0) st_acc(p.r, p.Nx, (long long)i * D + co(k), a);
+        __syncwarp();
+      }
     }
     for (long long q = ow; q < items; q += p.nOwn) {
       const int k = (int)(q / n), i = (int)(q - (long long)k * n);
       if (k != m) continue;
       if (p.resmask && !p.resmask[i]) continue;  // a row outside the sampled monitor
       // residual of stage m: r_m[i] - (A_0 dx_m)[i]
-      cmd<K, C> r, res;
+      cmd<K, C> ax, r, res;
+      warp_rowdot<K, C>(p.A0, p.NA0, row(0, i), ms, p.dx, p.Nx, n, D, co(m), ax);
       ld(p.r, p.Nx, (long long)i * D + co(k), r);
-      if constexpr (K >= 2) {
-        warp_rowdot_from<K, C>(p.A0, p.NA0, row(0, i), ms, p.dx, p.Nx, n, D, co(m), r, res);
-      } else {
-        cmd<K, C> ax;
-        warp_rowdot<K, C>(p.A0, p.NA0, row(0, i), ms, p.dx, p.Nx, n, D, co(m), ax);
-        cmd_sub(r, ax, res);
-      }
+      cmd_sub(r, ax, res);
       if (lane == 0) p.resabs[(long long)i * D + co(m)] = (C == 2) ? hypot(res.re[0], res.im[0]) : fabs(res.re[0]);
     }
   }
@@ -1646,16 +1599,9 @@ __global__ void stage0_kernel(FsubParams p) {
   const int n = p.n, D = p.D;
   if (i >= n) return;
   const int c0 = p.reverse ? D - 1 : 0;  // coefficient of stage 0
-  CAcc<K, C> acc;
-  cacc_zero(acc);
-  for (int l = lane; l < n; l += 32) {
-    cmd<K, C> w, b;
-    ld(p.W, p.Nnn, p.transpose ? (long long)l * n + i : (long long)i * n + l, w);
-    ld(p.rhs, p.Nx, (long long)l * D + c0, b);
-    cacc_fma(acc, w, b);
-  }
   cmd<K, C> s;
-  warp_sum_acc(acc, s);
+  warp_rowdot<K, C>(p.W, p.Nnn, p.transpose ? (long long)i : (long long)i * n, p.transpose ? n : 1, p.rhs, p.Nx, n, D,
+                    c0, s);
   if (p.rhs_sign < 0) {
     md_neg(s.re, s.re);
     md_neg(s.im, s.im);
@@ -1688,16 +1634,8 @@ __global__ void stage0y_kernel(FsubParams p) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int n = p.n, D = p.D;
   if (i >= n) return;
-  CAcc<K, C> acc;
-  cacc_zero(acc);
-  for (int l = lane; l < n; l += 32) {
-    cmd<K, C> y, b;
-    ld(p.Ys, p.Nnn, (long long)i * n + l, y);
-    ld(p.rhs, p.Nx, (long long)l * D, b);
-    cacc_fma(acc, y, b);
-  }
-  cmd<K, C> s;
-  warp_sum_acc(acc, s);
+  cmd<K, C> s;  // (Y b_0)_i
+  warp_rowdot<K, C>(p.Ys, p.Nnn, (long long)i * n, 1, p.rhs, p.Nx, n, D, 0, s);
   if (lane == 0) {
     cmd<K, C> b;
     ld(p.rhs, p.Nx, (long long)i * D, b);
@@ -1717,16 +1655,8 @@ __global__ void stage0z_kernel(FsubParams p) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int n = p.n, D = p.D;
   if (i >= n) return;
-  CAcc<K, C> acc;
-  cacc_zero(acc);
-  for (int l = i + lane; l < n; l += 32) {
-    cmd<K, C> z, t;
-    ld(p.Zs, p.Nnn, (long long)i * n + l, z);
-    ld(p.t0, n, l, t);
-    cacc_fma(acc, z, t);
-  }
-  cmd<K, C> s;
-  warp_sum_acc(acc, s);
+  cmd<K, C> s;  // sum over l >= i of Z_il t0_l (Z upper triangular)
+  warp_rowdot<K, C>(p.Zs, p.Nnn, (long long)i * n + i, 1, p.t0 + i, n, n - i, 1, 0, s);
   if (lane == 0) {
     st(p.dx, p.Nx, (long long)i * D, s);
     if (p.xnext0) {

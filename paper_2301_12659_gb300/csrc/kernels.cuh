@@ -20,6 +20,7 @@
 //   update kernels x += dx and the norms of the step.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include "md.cuh"
 #include "params.h"
 #include "xf.cuh"
@@ -773,10 +774,12 @@ __device__ __forceinline__ void dot_finish(xfn::xfacc<W>& ar, xfn::xfacc<W>& ai,
 }
 
 // The dataflow QR's warps and the pivot of the large-n QR are chains of
-// dependent operations on one warp, each run once per column: they call the
-// basic operations out of line (xf.cuh), so that their code stays in the
-// instruction cache.
-using QO = xfn::xf_ops_call;
+// dependent operations on one warp, each run once per column: from 4 words
+// up they call the basic operations out of line (xf.cuh), so that their code
+// stays in the instruction cache; at 1 and 2 words the inlined code is small
+// and the call would cost more than it saves.
+template <int W>
+using QOps = typename std::conditional<(W >= 4), xfn::xf_ops_call, xfn::xf_ops_inline>::type;
 
 // dot = sum of conj(x_j[i]) y[i] over rows i = j..n-1 (x_j from Vm); the
 // rows of x_j are also staged in the warp's shared buffer xs, where the
@@ -785,6 +788,7 @@ template <int K, int C>
 __device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const uint64_t* y, uint64_t* xs,
                                              cxf<xfn::xf_words_t<K>::value, C>& dot) {
   constexpr int W = xfn::xf_words_t<K>::value;
+  using QO = QOps<W>;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   int er = 2 * xfn::XF_ZERO_E, ei = er;
@@ -816,6 +820,7 @@ __device__ __forceinline__ void qr_lookahead(const QrParams& p, int j, const uin
 template <int K, int C>
 __device__ __forceinline__ void qr_norm2(const uint64_t* y, int n, int i0, xfn::xf<xfn::xf_words_t<K>::value>& nrm) {
   constexpr int W = xfn::xf_words_t<K>::value;
+  using QO = QOps<W>;
   const int lane = threadIdx.x & 31;
   int er = 2 * xfn::XF_ZERO_E, ei = er;
   for (int i = i0 + lane; i < n; i += 32) {
@@ -842,6 +847,7 @@ __device__ __forceinline__ void qr_form_w(const QrParams& p, int j, const uint64
                                           const cxf<xfn::xf_words_t<K>::value, C>& dot,
                                           cxf<xfn::xf_words_t<K>::value, C>& w) {
   constexpr int W = xfn::xf_words_t<K>::value;
+  using QO = QOps<W>;
   cxf<W, C> sa, yj;
   xld<W, C>(p.salpha, p.n, j, sa);
   xld<W, C>(y, p.n, j, yj);
@@ -859,6 +865,7 @@ template <int K, int C>
 __device__ __forceinline__ void qr_update(const QrParams& p, int j, uint64_t* y, const uint64_t* xs,
                                           const cxf<xfn::xf_words_t<K>::value, C>& w, int pub = -1) {
   constexpr int W = xfn::xf_words_t<K>::value;
+  using QO = QOps<W>;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   cxf<W, 1> tau;
@@ -897,6 +904,7 @@ template <int K, int C>
 __device__ void qr_column(const QrParams& p, int c, uint64_t* y, uint64_t* xs, unsigned ep) {
   using namespace xfn;
   constexpr int W = xf_words_t<K>::value;
+  using QO = QOps<W>;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   unsigned* fcol = p.flags;
@@ -1062,6 +1070,7 @@ __device__ void qr_identity(const QrParams& p, int e, uint64_t* y, uint64_t* xs,
 template <int K, int C>
 __device__ void qr_rinv_rows(const QrParams& p, int ia, int ib, uint64_t* za, uint64_t* zb, unsigned ep) {
   constexpr int W = xfn::xf_words_t<K>::value;
+  using QO = QOps<W>;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   unsigned* frinv = p.flags + 2 * n;
@@ -1169,6 +1178,7 @@ template <int K, int C>
 __device__ void qrg_pivot(const QrParams& p, int j) {
   using namespace xfn;
   constexpr int W = xf_words_t<K>::value;
+  using QO = QOps<W>;
   const int lane = threadIdx.x & 31;
   const int n = p.n;
   const long long nn = (long long)n * n;

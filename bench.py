@@ -106,12 +106,13 @@ def parse():
 
 
 # DRAM bytes (read + write) per launch of the phase's main kernel from one ncu
-# capture of the unchanged kernels (profiles/ncu_qr_ed_fsub_qd-real-n64-d31.md);
-# absent entries report null.
+# capture of the unchanged kernels (profiles/ncu_qr_ed_fsub_qd-real-n64-d31.md:
+# qr_kernel and fsub_kernel as they are now, ed_kernel from the earlier
+# capture, unchanged since); absent entries report null.
 NCU_TRAFFIC = {
-    ("qd-real-n64-d31", "qr"): 540544,
+    ("qd-real-n64-d31", "qr"): 438016 + 2816,
     ("qd-real-n64-d31", "evaluate"): 1294976,
-    ("qd-real-n64-d31", "forward"): 4646400 + 27264,
+    ("qd-real-n64-d31", "forward"): 4722944 + 6144,
 }
 
 

@@ -1374,8 +1374,12 @@ __global__ void qrg_bsub_kernel(QrParams p) {
   }
 }
 
+template <int K, int C>
+__device__ __forceinline__ void warp_rowdot(const double* Mp, long long NM, long long row_off, int ms,
+                                            const double* xp, long long Nx, int n, int D, int kx, cmd<K, C>& out);
+
 // W = Z Y = R^{-1} Q^H: one warp per entry, lanes over k >= i (Z is upper
-// triangular), over the whole GPU.
+// triangular), one fixed-point row product each, over the whole GPU.
 template <int K, int C>
 __global__ void w_kernel(QrParams p) {
   const int n = p.n;
@@ -1385,16 +1389,8 @@ __global__ void w_kernel(QrParams p) {
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long t = wid; t < nn; t += nw) {
     const int i = (int)(t / n), e = (int)(t - (long long)i * n);
-    CAcc<K, C> acc;
-    cacc_zero(acc);
-    for (int k = i + lane; k < n; k += 32) {
-      cmd<K, C> z, yv;
-      ld(p.Z, p.Nnn, (long long)i * n + k, z);
-      ld(p.Y, p.Nnn, (long long)k * n + e, yv);
-      cacc_fma(acc, z, yv);
-    }
-    cmd<K, C> w;
-    warp_sum_acc(acc, w);
+    cmd<K, C> w;  // sum over k >= i of Z_ik Y_ke (Z upper triangular): column e of Y from row i
+    warp_rowdot<K, C>(p.Z, p.Nnn, (long long)i * n + i, 1, p.Y + (long long)i * n, p.Nnn, n - i, n, e, w);
     if (lane == 0) st(p.W, p.Nnn, t, w);
   }
 }

@@ -130,3 +130,35 @@ extern "C" void xf_host_add_count(int count, const uint64_t* vals, uint64_t s0, 
   out[0] = s;
   out[1] = c;
 }
+
+// Columns LO .. NA+NB-1 of the product of two word arrays (mul_top); out
+// receives NA+NB-LO words.  Returns 1 for a shape not instantiated here.
+template <int NA, int NB, int LO>
+static void mtop(const uint64_t* a, const uint64_t* b, uint64_t* out) {
+  uint64_t x[NA], y[NB], r[NA + NB - LO];
+  for (int i = 0; i < NA; ++i) x[i] = a[i];
+  for (int i = 0; i < NB; ++i) y[i] = b[i];
+  mul_top<NA, NB, LO>(x, y, r);
+  for (int i = 0; i < NA + NB - LO; ++i) out[i] = r[i];
+}
+
+extern "C" int xf_host_mul_top(int NA, int NB, int LO, const uint64_t* a, const uint64_t* b, uint64_t* out) {
+  const int key = NA * 100 + NB * 10 + LO;
+  switch (key) {
+    case 110: mtop<1, 1, 0>(a, b, out); return 0;
+    case 121: mtop<1, 2, 1>(a, b, out); return 0;
+    case 221: mtop<2, 2, 1>(a, b, out); return 0;
+    case 222: mtop<2, 2, 2>(a, b, out); return 0;
+    case 232: mtop<2, 3, 2>(a, b, out); return 0;
+    case 332: mtop<3, 3, 2>(a, b, out); return 0;
+    case 333: mtop<3, 3, 3>(a, b, out); return 0;
+    case 343: mtop<3, 4, 3>(a, b, out); return 0;
+    case 443: mtop<4, 4, 3>(a, b, out); return 0;
+    case 444: mtop<4, 4, 4>(a, b, out); return 0;
+    case 454: mtop<4, 5, 4>(a, b, out); return 0;
+    case 776: mtop<7, 7, 6>(a, b, out); return 0;
+    case 777: mtop<7, 7, 7>(a, b, out); return 0;
+    case 787: mtop<7, 8, 7>(a, b, out); return 0;
+  }
+  return 1;
+}

@@ -264,3 +264,42 @@ def test_column_sum_with_counted_carries(lib):
             lib.xf_host_add_count(count, vals.ctypes.data_as(P), s0, 5, out.ctypes.data_as(P))
             total = s0 + 5 * 2**64 + sum(int(v) for v in vals)
             assert int(out[0]) + (int(out[1]) << 64) == total
+
+
+# the shapes the fixed-point Newton steps use at widths V = 1, 2, 3, 4, 7:
+# (V, V, V-1), (V, V, V) and (V, V+1, V)
+MUL_TOP_SHAPES = [(1, 1, 0), (1, 2, 1), (2, 2, 1), (2, 2, 2), (2, 3, 2), (3, 3, 2), (3, 3, 3), (3, 4, 3),
+                  (4, 4, 3), (4, 4, 4), (4, 5, 4), (7, 7, 6), (7, 7, 7), (7, 8, 7)]
+
+
+@pytest.mark.parametrize("shape", MUL_TOP_SHAPES)
+def test_mul_top_against_integer_products(lib, shape):
+    """mul_top (the truncated word product of the fixed-point reciprocal and
+    reciprocal square root) against the exact product of Python integers:
+    the columns from LO up, the lowest short by fewer than NA + NB units
+    (only column LO-1's products enter below it) and never above the exact
+    value.  Operands: random words, all-ones words (every carry runs) and
+    sparse words."""
+    NA, NB, LO = shape
+    nout = NA + NB - LO
+    rng = np.random.default_rng(1200 + 100 * NA + 10 * NB + LO)
+    full = (1 << 64) - 1
+    cases = [(rng.integers(0, 2 ** 63, size=NA, dtype=np.uint64) * np.uint64(2) + np.uint64(1),
+              rng.integers(0, 2 ** 63, size=NB, dtype=np.uint64) * np.uint64(2) + np.uint64(1)) for _ in range(60)]
+    cases.append((np.full(NA, full, dtype=np.uint64), np.full(NB, full, dtype=np.uint64)))
+    cases.append((np.array([0] * (NA - 1) + [1 << 63], dtype=np.uint64), np.full(NB, full, dtype=np.uint64)))
+    cases.append((np.array([1] + [0] * (NA - 1), dtype=np.uint64), np.array([0] * (NB - 1) + [1], dtype=np.uint64)))
+    fn = lib.xf_host_mul_top
+    fn.restype = ctypes.c_int
+    pu = ctypes.POINTER(ctypes.c_uint64)
+    for a, b in cases:
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        out = np.zeros(nout, dtype=np.uint64)
+        assert fn(NA, NB, LO, a.ctypes.data_as(pu), b.ctypes.data_as(pu), out.ctypes.data_as(pu)) == 0
+        A = sum(int(w) << (64 * i) for i, w in enumerate(a))
+        B = sum(int(w) << (64 * i) for i, w in enumerate(b))
+        exact = (A * B) >> (64 * LO)
+        got = sum(int(w) << (64 * i) for i, w in enumerate(out))
+        assert 0 <= exact - got < NA + NB, (shape, exact - got)
+

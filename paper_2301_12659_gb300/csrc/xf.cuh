@@ -821,15 +821,6 @@ XF_FN double xf_mant_double(const xf<W>& a) {
   return bitsd((1023ULL << 52) | ((top >> 11) & 0xfffffffffffffULL));
 }
 
-// a at another width: the leading min(W1, W2) words, zero extended
-template <int W2, int W1>
-XF_FN void xf_resize(const xf<W1>& a, xf<W2>& r) {
-#pragma unroll
-  for (int i = 0; i < W2; ++i) r.m[W2 - 1 - i] = i < W1 ? a.m[W1 - 1 - i] : 0ULL;
-  r.e = a.e;
-  r.s = a.s;
-}
-
 // ---------------------------------------------------------------------------
 // reciprocal and reciprocal square root: Newton's iteration in fixed point
 // ---------------------------------------------------------------------------
